@@ -1,0 +1,810 @@
+// dwf_api.cu -- the C ABI of libdwf: handle, 5th-dimension matrices, gauge
+// loading, the D_bb / D_bb^dagger applies, the propagator solve and the force.
+//
+// Operator factorisation (Sec. 2 Eq. mobius1 with Eq. coeff and Eq. wilson):
+// D_alpha = D_w B + C with B, C real Ls x Ls matrices acting on the 5th index of
+// each chirality (B: D_w -> 1, C: D_w -> 0 in the block list).  With
+// D_w = (4 + M5) - H/2 (H the Wilson hopping term) the site-local part is
+// I = (4 + M5) B + C and the hopping part is -1/2 H B, so the red-black operator
+// of Sec. 3 Eq. redblack becomes
+//     D_bb = 1 - 1/4 I^-1 H_br K H_rb B,          K = B I^-1,
+//     D_bb^+ = gamma5 [1 - 1/4 B^T H_br K^T H_rb I^-T] gamma5.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/dwf.h"
+#include "dwf_internal.cuh"
+
+using namespace dwf;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Real Ls x Ls matrices of one (alpha, m) for both chiralities, FP64 host copy
+// and device copies in FP64 and FP32.  Device layout (in elements):
+//   K[2][Ls][Ls] KT IinvM IinvT Ifull BT  then Bdiag[2][Ls] Boff[2][Ls]
+struct MatSet {
+  double alpha = 1.0, m = 0.0;
+  int Ls = 0;
+  std::vector<double> host;
+  void* dev[2] = {nullptr, nullptr};  // [0] double, [1] float
+  enum { K = 0, KT = 1, IINV = 2, IINVT = 3, IFULL = 4, BT = 5, NMAT = 6 };
+  size_t mat_off(int which) const { return (size_t)which * 2 * Ls * Ls; }
+  size_t bdiag_off() const { return (size_t)NMAT * 2 * Ls * Ls; }
+  size_t boff_off() const { return bdiag_off() + 2 * (size_t)Ls; }
+  size_t count() const { return boff_off() + 2 * (size_t)Ls; }
+  const void* ptr(int prec, size_t off) const {
+    const int f = prec == P64 ? 0 : 1;
+    const size_t es = f == 0 ? 8 : 4;
+    return reinterpret_cast<const char*>(dev[f]) + off * es;
+  }
+};
+
+bool invert(std::vector<double> a, int n, std::vector<double>& inv) {
+  // Gauss-Jordan elimination with partial pivoting.
+  inv.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; i++) inv[(size_t)i * n + i] = 1.0;
+  for (int col = 0; col < n; col++) {
+    int piv = col;
+    for (int r = col + 1; r < n; r++)
+      if (std::fabs(a[(size_t)r * n + col]) > std::fabs(a[(size_t)piv * n + col])) piv = r;
+    if (a[(size_t)piv * n + col] == 0.0) return false;
+    if (piv != col)
+      for (int k = 0; k < n; k++) {
+        std::swap(a[(size_t)piv * n + k], a[(size_t)col * n + k]);
+        std::swap(inv[(size_t)piv * n + k], inv[(size_t)col * n + k]);
+      }
+    const double d = 1.0 / a[(size_t)col * n + col];
+    for (int k = 0; k < n; k++) {
+      a[(size_t)col * n + k] *= d;
+      inv[(size_t)col * n + k] *= d;
+    }
+    for (int r = 0; r < n; r++) {
+      if (r == col) continue;
+      const double f = a[(size_t)r * n + col];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; k++) {
+        a[(size_t)r * n + k] -= f * a[(size_t)col * n + k];
+        inv[(size_t)r * n + k] -= f * inv[(size_t)col * n + k];
+      }
+    }
+  }
+  return true;
+}
+
+// B_+-, C_+- of Eq. mobius1: row s of the P_+ (chir 0) and P_- (chir 1) blocks.
+// fb = b (B) or 1 (C); fc = c (B) or -1 (C).
+void chiral_blocks(int Ls, double alpha, double m, const double* fb, const double* fc,
+                   std::vector<double>& Mp, std::vector<double>& Mm) {
+  Mp.assign((size_t)Ls * Ls, 0.0);
+  Mm.assign((size_t)Ls * Ls, 0.0);
+  auto P = [&](int r, int c) -> double& { return Mp[(size_t)r * Ls + c]; };
+  auto M = [&](int r, int c) -> double& { return Mm[(size_t)r * Ls + c]; };
+  const int l = Ls - 1;
+  // row 1: D_1+(P_- + alpha P_+), alpha D_1- P_- (col 2), -m D_1- P_+ (col Ls)
+  P(0, 0) += alpha * fb[0];
+  M(0, 0) += fb[0];
+  M(0, 1) += alpha * fc[0];
+  P(0, l) += -m * fc[0];
+  // rows 2 .. Ls-1: alpha D_i- P_+ (col i-1), alpha D_i+ (col i), alpha D_i- P_- (col i+1)
+  for (int i = 1; i < l; i++) {
+    P(i, i - 1) += alpha * fc[i];
+    P(i, i) += alpha * fb[i];
+    M(i, i) += alpha * fb[i];
+    M(i, i + 1) += alpha * fc[i];
+  }
+  // row Ls: -m D_Ls- P_- (col 1), alpha D_Ls- P_+ (col Ls-1), D_Ls+(P_+ + alpha P_-)
+  M(l, 0) += -m * fc[l];
+  P(l, l - 1) += alpha * fc[l];
+  P(l, l) += fb[l];
+  M(l, l) += alpha * fb[l];
+}
+
+std::vector<double> matmul(const std::vector<double>& a, const std::vector<double>& b, int n) {
+  std::vector<double> c((size_t)n * n, 0.0);
+  for (int i = 0; i < n; i++)
+    for (int k = 0; k < n; k++)
+      for (int j = 0; j < n; j++) c[(size_t)i * n + j] += a[(size_t)i * n + k] * b[(size_t)k * n + j];
+  return c;
+}
+
+std::vector<double> transpose(const std::vector<double>& a, int n) {
+  std::vector<double> t((size_t)n * n);
+  for (int i = 0; i < n; i++)
+    for (int j = 0; j < n; j++) t[(size_t)j * n + i] = a[(size_t)i * n + j];
+  return t;
+}
+
+}  // namespace
+
+struct dwf_ctx {
+  Geom g{};
+  int Ls = 0;
+  double M5 = 0, m = 0, alpha = 1;
+  std::vector<double> b, c;
+  dwf_options opt{};
+  int device = 0;
+  std::string err;
+  std::map<std::pair<double, double>, MatSet> mats;
+  void* gauge[3] = {nullptr, nullptr, nullptr};  // FP64, FP32, FP16
+  bool gauge_loaded = false;
+  std::vector<void*> allocs;
+  // workspace
+  std::map<std::string, void*> ws;
+  std::map<std::string, size_t> ws_size;
+  double* scal = nullptr;          // per-rhs scalars, kScal doubles each
+  double* partial = nullptr;       // reduction partials
+  unsigned int* counter = nullptr; // reduction counters
+  int partial_stride = 0;
+  int scal_rhs = 0;
+  double* pinned = nullptr;        // host mirror of scal
+};
+
+namespace {
+
+constexpr int kScal = 16;
+enum { S_ZZ0 = 0, S_ZZ1 = 1, S_WW = 2, S_RR = 3, S_RRHI = 4, S_BB = 5, S_T0 = 6, S_T1 = 7, S_T2 = 8 };
+
+int fail(dwf_ctx* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+#define CUCHK(h, expr)                                                                       \
+  do {                                                                                      \
+    cudaError_t _e = (expr);                                                                \
+    if (_e != cudaSuccess)                                                                  \
+      return fail(h, _e == cudaErrorMemoryAllocation ? DWF_ERR_OOM : DWF_ERR_CUDA,         \
+                  std::string(#expr) + ": " + cudaGetErrorString(_e));                      \
+  } while (0)
+
+bool valid_prec(int p) { return p >= DWF_FP64 && p <= DWF_BF16; }
+
+int build_matset(dwf_ctx* h, double alpha, double m, MatSet** out) {
+  auto key = std::make_pair(alpha, m);
+  auto it = h->mats.find(key);
+  if (it != h->mats.end()) {
+    *out = &it->second;
+    return DWF_OK;
+  }
+  const int Ls = h->Ls;
+  MatSet ms;
+  ms.alpha = alpha;
+  ms.m = m;
+  ms.Ls = Ls;
+  std::vector<double> ones(Ls, 1.0), mones(Ls, -1.0);
+  std::vector<double> Bm[2], Cm[2];
+  chiral_blocks(Ls, alpha, m, h->b.data(), h->c.data(), Bm[0], Bm[1]);
+  chiral_blocks(Ls, alpha, m, ones.data(), mones.data(), Cm[0], Cm[1]);
+  ms.host.assign(ms.count(), 0.0);
+  const size_t LL = (size_t)Ls * Ls;
+  for (int ch = 0; ch < 2; ch++) {
+    std::vector<double> I(LL), Iinv;
+    for (size_t k = 0; k < LL; k++) I[k] = (4.0 + h->M5) * Bm[ch][k] + Cm[ch][k];
+    if (!invert(I, Ls, Iinv))
+      return fail(h, DWF_ERR_INVALID_ARG, "the site-local matrix I = (4+M5)B + C is singular");
+    std::vector<double> K = matmul(Bm[ch], Iinv, Ls);
+    std::vector<double> mats[MatSet::NMAT] = {K, transpose(K, Ls), Iinv, transpose(Iinv, Ls), I,
+                                              transpose(Bm[ch], Ls)};
+    for (int w = 0; w < MatSet::NMAT; w++)
+      std::copy(mats[w].begin(), mats[w].end(), ms.host.begin() + ms.mat_off(w) + ch * LL);
+    // cyclic bidiagonal form of B
+    for (int s = 0; s < Ls; s++) {
+      const int col = ch == 0 ? (s + Ls - 1) % Ls : (s + 1) % Ls;
+      for (int q = 0; q < Ls; q++) {
+        if (q == s || q == col) continue;
+        if (Bm[ch][(size_t)s * Ls + q] != 0.0)
+          return fail(h, DWF_ERR_STATE, "B is not cyclic bidiagonal");
+      }
+      ms.host[ms.bdiag_off() + ch * Ls + s] = Bm[ch][(size_t)s * Ls + s];
+      ms.host[ms.boff_off() + ch * Ls + s] = Ls == 1 ? 0.0 : Bm[ch][(size_t)s * Ls + col];
+    }
+  }
+  std::vector<float> hf(ms.count());
+  for (size_t k = 0; k < hf.size(); k++) hf[k] = (float)ms.host[k];
+  CUCHK(h, cudaMalloc(&ms.dev[0], ms.count() * 8));
+  CUCHK(h, cudaMalloc(&ms.dev[1], ms.count() * 4));
+  CUCHK(h, cudaMemcpy(ms.dev[0], ms.host.data(), ms.count() * 8, cudaMemcpyHostToDevice));
+  CUCHK(h, cudaMemcpy(ms.dev[1], hf.data(), ms.count() * 4, cudaMemcpyHostToDevice));
+  h->allocs.push_back(ms.dev[0]);
+  h->allocs.push_back(ms.dev[1]);
+  auto res = h->mats.emplace(key, std::move(ms));
+  *out = &res.first->second;
+  return DWF_OK;
+}
+
+int get_ws(dwf_ctx* h, const std::string& name, size_t bytes, void** out) {
+  auto it = h->ws.find(name);
+  if (it != h->ws.end() && h->ws_size[name] >= bytes) {
+    *out = it->second;
+    return DWF_OK;
+  }
+  if (it != h->ws.end()) {
+    cudaFree(it->second);
+    h->ws.erase(it);
+  }
+  void* p = nullptr;
+  CUCHK(h, cudaMalloc(&p, bytes));
+  h->ws[name] = p;
+  h->ws_size[name] = bytes;
+  *out = p;
+  return DWF_OK;
+}
+
+int ensure_reduce(dwf_ctx* h, int nrhs) {
+  const int need_blocks =
+      std::max(hop_grid_blocks(h->g, P64, 0), std::max(hop_grid_blocks(h->g, P32, 0),
+                                                       blas_grid_blocks(h->g)));
+  if (h->scal && h->scal_rhs >= nrhs && h->partial_stride >= need_blocks) return DWF_OK;
+  if (h->scal) {
+    cudaFree(h->scal);
+    cudaFree(h->partial);
+    cudaFree(h->counter);
+    cudaFreeHost(h->pinned);
+  }
+  h->scal_rhs = std::max(nrhs, 1);
+  h->partial_stride = need_blocks;
+  CUCHK(h, cudaMalloc(&h->scal, sizeof(double) * kScal * h->scal_rhs));
+  CUCHK(h, cudaMalloc(&h->partial, sizeof(double) * (size_t)need_blocks * h->scal_rhs * 4));
+  CUCHK(h, cudaMalloc(&h->counter, sizeof(unsigned int) * h->scal_rhs * 4));
+  CUCHK(h, cudaMemset(h->counter, 0, sizeof(unsigned int) * h->scal_rhs * 4));
+  CUCHK(h, cudaMemset(h->scal, 0, sizeof(double) * kScal * h->scal_rhs));
+  CUCHK(h, cudaMallocHost(&h->pinned, sizeof(double) * kScal * h->scal_rhs));
+  return DWF_OK;
+}
+
+// Reduction slot k (0..3) into scalar index which.
+Reduce make_reduce(dwf_ctx* h, int slot, int which) {
+  Reduce r;
+  r.partial = h->partial + (size_t)slot * h->partial_stride * h->scal_rhs;
+  r.counter = h->counter + (size_t)slot * h->scal_rhs;
+  r.result = h->scal + which;
+  r.partial_stride = h->partial_stride;
+  r.result_stride = kScal;
+  return r;
+}
+
+const void* gauge_for(dwf_ctx* h, int prec) {
+  return prec == P64 ? h->gauge[0] : (prec == P32 ? h->gauge[1] : h->gauge[2]);
+}
+
+HopLaunch base_hop(dwf_ctx* h, int prec, int p, int nrhs, size_t stride) {
+  HopLaunch L{};
+  L.prec = prec;
+  L.p = p;
+  L.nrhs = nrhs;
+  L.stride = stride;
+  L.gauge = gauge_for(h, prec);
+  L.gauge_parity_bytes = gauge_bytes(h->g, prec) / 2;
+  L.c_hop = 1.0;
+  L.c_loc = 0.0;
+  return L;
+}
+
+// out = D_bb in.  tmp: red half-field(s) of the same precision.
+int apply_dbb(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void* in, void* tmp, int nrhs,
+              const Reduce* norm, cudaStream_t s) {
+  const int black = h->opt.rb_parity, red = 1 - black;
+  const size_t st = field_bytes(h->g, prec);
+  HopLaunch A = base_hop(h, prec, red, nrhs, st);
+  A.out = tmp;
+  A.v = in;
+  A.pre = PRE_B;
+  A.pre_diag = ms.ptr(prec, ms.bdiag_off());
+  A.pre_off = ms.ptr(prec, ms.boff_off());
+  A.post = ms.ptr(prec, ms.mat_off(MatSet::K));
+  CUCHK(h, launch_hop(h->g, A, s));
+  HopLaunch B = base_hop(h, prec, black, nrhs, st);
+  B.out = out;
+  B.v = tmp;
+  B.w = in;
+  B.post = ms.ptr(prec, ms.mat_off(MatSet::IINV));
+  B.loc = LOC_ID;
+  B.c_hop = -0.25;
+  B.c_loc = 1.0;
+  B.red = norm;
+  CUCHK(h, launch_hop(h->g, B, s));
+  return DWF_OK;
+}
+
+// out = D_bb^+ in.  tmp_red: red field(s); tmp_blk: black field(s).
+int apply_dbb_dag(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void* in, void* tmp_red,
+                  void* tmp_blk, int nrhs, const Reduce* norm, cudaStream_t s) {
+  const int black = h->opt.rb_parity, red = 1 - black;
+  const size_t st = field_bytes(h->g, prec);
+  LocalLaunch L{};
+  L.prec = prec;
+  L.out = tmp_blk;
+  L.in = in;
+  L.stride = st;
+  L.nrhs = nrhs;
+  L.m = ms.ptr(prec, ms.mat_off(MatSet::IINVT));
+  L.c = 1.0;
+  L.g5in = 1;
+  CUCHK(h, launch_local(h->g, L, s));
+  HopLaunch A = base_hop(h, prec, red, nrhs, st);
+  A.out = tmp_red;
+  A.v = tmp_blk;
+  A.post = ms.ptr(prec, ms.mat_off(MatSet::KT));
+  CUCHK(h, launch_hop(h->g, A, s));
+  HopLaunch B = base_hop(h, prec, black, nrhs, st);
+  B.out = out;
+  B.v = tmp_red;
+  B.w = in;
+  B.post = ms.ptr(prec, ms.mat_off(MatSet::BT));
+  B.loc = LOC_ID;
+  B.c_hop = -0.25;
+  B.c_loc = 1.0;
+  B.g5out = 1;
+  B.red = norm;
+  CUCHK(h, launch_hop(h->g, B, s));
+  return DWF_OK;
+}
+
+// (out0, out1) = D_alpha(ms) (in0, in1), FP64 internal halves by parity.
+int apply_dalpha_halves(dwf_ctx* h, const MatSet& ms, void* out[2], const void* in[2], cudaStream_t s) {
+  const size_t st = field_bytes(h->g, P64);
+  for (int p = 0; p < 2; p++) {
+    HopLaunch L = base_hop(h, P64, p, 1, st);
+    L.out = out[p];
+    L.v = in[1 - p];
+    L.w = in[p];
+    L.pre = PRE_B;
+    L.pre_diag = ms.ptr(P64, ms.bdiag_off());
+    L.pre_off = ms.ptr(P64, ms.boff_off());
+    L.loc = LOC_DENSE;
+    L.locm = ms.ptr(P64, ms.mat_off(MatSet::IFULL));
+    L.c_hop = -0.5;
+    L.c_loc = 1.0;
+    CUCHK(h, launch_hop(h->g, L, s));
+  }
+  return DWF_OK;
+}
+
+int sync_read(dwf_ctx* h, int nrhs, cudaStream_t s) {
+  CUCHK(h, cudaMemcpyAsync(h->pinned, h->scal, sizeof(double) * kScal * nrhs, cudaMemcpyDeviceToHost, s));
+  CUCHK(h, cudaStreamSynchronize(s));
+  return DWF_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct SolveWork {
+  void *b_hi, *x_hi, *r_hi, *t64, *t64r;  // FP64 black (t64r red)
+  void *p, *r, *w, *z, *xlo, *tb, *tr;    // inner precision
+};
+
+int alloc_solve_work(dwf_ctx* h, int prec, SolveWork& W) {
+  const size_t f64 = field_bytes(h->g, P64), fi = field_bytes(h->g, prec);
+  const std::string sfx = "_" + std::to_string(prec);
+  int rc;
+  if ((rc = get_ws(h, "b_hi", f64, &W.b_hi))) return rc;
+  if ((rc = get_ws(h, "x_hi", f64, &W.x_hi))) return rc;
+  if ((rc = get_ws(h, "r_hi", f64, &W.r_hi))) return rc;
+  if ((rc = get_ws(h, "t64", f64, &W.t64))) return rc;
+  if ((rc = get_ws(h, "t64r", f64, &W.t64r))) return rc;
+  if ((rc = get_ws(h, "p" + sfx, fi, &W.p))) return rc;
+  if ((rc = get_ws(h, "r" + sfx, fi, &W.r))) return rc;
+  if ((rc = get_ws(h, "w" + sfx, fi, &W.w))) return rc;
+  if ((rc = get_ws(h, "z" + sfx, fi, &W.z))) return rc;
+  if ((rc = get_ws(h, "xlo" + sfx, fi, &W.xlo))) return rc;
+  if ((rc = get_ws(h, "tb" + sfx, fi, &W.tb))) return rc;
+  if ((rc = get_ws(h, "tr" + sfx, fi, &W.tr))) return rc;
+  return DWF_OK;
+}
+
+// CG on D^+ D x = D^+ b (CGNR form: r = b - D x is tracked, z = D^+ r), inner
+// precision prec with FP64 reliable updates (residual replacement when |r|
+// drops below delta times its maximum since the last update) or, with
+// restart = true, FP64 defect correction (the inner CG restarts from p = z
+// after every update).  b_hi, x_hi: FP64 black fields; x_hi returned.
+int cgnr_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxiter, double delta,
+               bool restart, SolveWork& W, dwf_stats* st, cudaStream_t s) {
+  const size_t f64 = field_bytes(h->g, P64), fi = field_bytes(h->g, prec);
+  Reduce red_ww = make_reduce(h, 0, S_WW), red_rr = make_reduce(h, 1, S_RR);
+  Reduce red_zz[2] = {make_reduce(h, 2, S_ZZ0), make_reduce(h, 2, S_ZZ1)};
+  Reduce red_hi = make_reduce(h, 3, S_RRHI), red_bb = make_reduce(h, 3, S_BB);
+  int rc;
+  CUCHK(h, cudaMemsetAsync(W.x_hi, 0, f64, s));
+  CUCHK(h, cudaMemsetAsync(W.xlo, 0, fi, s));
+  CUCHK(h, launch_convert(h->g, P64, W.r_hi, P64, W.b_hi, 1, f64, f64, &red_bb, s));
+  CUCHK(h, launch_convert(h->g, prec, W.r, P64, W.b_hi, 1, fi, f64, nullptr, s));
+  if ((rc = sync_read(h, 1, s))) return rc;
+  const double bb = h->pinned[S_BB];
+  if (!(bb > 0.0)) {
+    if (st) {
+      st->iterations = 0;
+      st->restarts = 0;
+      st->true_resid = 0.0;
+    }
+    return bb == 0.0 ? DWF_OK : fail(h, DWF_ERR_BREAKDOWN, "source norm is not finite");
+  }
+  const double bnorm = std::sqrt(bb);
+  int cur = 0;
+  if ((rc = apply_dbb_dag(h, ms, prec, W.z, W.r, W.tr, W.tb, 1, &red_zz[cur], s))) return rc;
+  CUCHK(h, cudaMemcpyAsync(W.p, W.z, fi, cudaMemcpyDeviceToDevice, s));
+  double rmax = bnorm;
+  int it = 0, restarts = 0;
+  double true_res = 1.0;
+  bool converged = false;
+  const int check = std::max(1, h->opt.check_every);
+  while (it < maxiter) {
+    if ((rc = apply_dbb(h, ms, prec, W.w, W.p, W.tr, 1, &red_ww, s))) return rc;
+    CUCHK(h, launch_xr_update(h->g, prec, W.xlo, W.r, W.p, W.w, h->scal + (cur ? S_ZZ1 : S_ZZ0),
+                              h->scal + S_WW, kScal, 1, fi, &red_rr, s));
+    it++;
+    if (it % check == 0 || it >= maxiter) {
+      if ((rc = sync_read(h, 1, s))) return rc;
+      const double rr = h->pinned[S_RR], ww = h->pinned[S_WW];
+      if (!std::isfinite(rr) || !std::isfinite(ww) || !(ww > 0.0))
+        return fail(h, DWF_ERR_BREAKDOWN, "CG breakdown (|Dp|^2 <= 0 or not finite)");
+      const double rn = std::sqrt(rr);
+      if (rn < delta * rmax || rn <= tol * bnorm || it >= maxiter) {
+        // reliable update: x_hi += x_lo, r = b - D x_hi in FP64
+        CUCHK(h, launch_accumulate64(h->g, W.x_hi, prec, W.xlo, 1, 1, f64, fi, s));
+        if ((rc = apply_dbb(h, ms, P64, W.t64, W.x_hi, W.t64r, 1, nullptr, s))) return rc;
+        CUCHK(h, launch_sub64_norm(h->g, W.r_hi, W.b_hi, W.t64, 1, f64, &red_hi, s));
+        CUCHK(h, launch_convert(h->g, prec, W.r, P64, W.r_hi, 1, fi, f64, nullptr, s));
+        if ((rc = sync_read(h, 1, s))) return rc;
+        true_res = std::sqrt(h->pinned[S_RRHI]) / bnorm;
+        rmax = std::sqrt(h->pinned[S_RRHI]);
+        restarts++;
+        if (true_res <= tol) {
+          converged = true;
+          break;
+        }
+        if (it >= maxiter) break;
+        if (restart) {
+          cur = 0;
+          if ((rc = apply_dbb_dag(h, ms, prec, W.z, W.r, W.tr, W.tb, 1, &red_zz[cur], s))) return rc;
+          CUCHK(h, cudaMemcpyAsync(W.p, W.z, fi, cudaMemcpyDeviceToDevice, s));
+          continue;
+        }
+      }
+    }
+    const int nxt = 1 - cur;
+    if ((rc = apply_dbb_dag(h, ms, prec, W.z, W.r, W.tr, W.tb, 1, &red_zz[nxt], s))) return rc;
+    CUCHK(h, launch_p_update(h->g, prec, W.p, W.z, h->scal + (nxt ? S_ZZ1 : S_ZZ0),
+                             h->scal + (cur ? S_ZZ1 : S_ZZ0), kScal, 1, fi, s));
+    cur = nxt;
+  }
+  if (st) {
+    st->iterations = it;
+    st->restarts = restarts;
+    st->true_resid = true_res;
+  }
+  if (!converged) return fail(h, DWF_ERR_NOT_CONVERGED, "CG did not reach the tolerance within maxiter");
+  return DWF_OK;
+}
+
+int solver_params(dwf_ctx* h, int* prec, double* delta, bool* restart) {
+  *prec = h->opt.precision_inner;
+  *delta = h->opt.reliable_delta;
+  *restart = false;
+  if (h->opt.solver == DWF_SOLVER_FP64) {
+    *prec = P64;
+    *delta = 0.0;
+  } else if (h->opt.solver == DWF_SOLVER_DEFECT) {
+    *restart = true;
+  }
+  return DWF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dwf_default_options(dwf_options* opt) {
+  if (!opt) return DWF_ERR_INVALID_ARG;
+  opt->precision_inner = DWF_FP32;
+  opt->rb_parity = 0;
+  opt->bc_t = 1;
+  opt->rel_tol = 1e-10;
+  opt->maxiter = 100000;
+  opt->reliable_delta = 0.1;
+  opt->solver = DWF_SOLVER_RELIABLE;
+  opt->check_every = 16;
+  return DWF_OK;
+}
+
+int dwf_create(dwf_handle* out, const int lattice[4], int Ls, double M5, double m, double alpha,
+               const double* b, const double* c, const dwf_options* opt) {
+  if (!out || !lattice || !b || !c) return fail(nullptr, DWF_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  for (int k = 0; k < 4; k++)
+    if (lattice[k] < 2 || lattice[k] % 2)
+      return fail(nullptr, DWF_ERR_INVALID_ARG, "lattice extents must be even and >= 2");
+  if (Ls < 2 || Ls > kMaxLs) return fail(nullptr, DWF_ERR_INVALID_ARG, "Ls must be in [2, 32]");
+  const double V = (double)lattice[0] * lattice[1] * lattice[2] * lattice[3];
+  if (V / 2 * Ls * 24 > 2147483647.0)
+    return fail(nullptr, DWF_ERR_INVALID_ARG, "lattice too large for 32-bit 5D indexing");
+  dwf_ctx* h = new dwf_ctx();
+  for (int k = 0; k < 4; k++) h->g.L[k] = lattice[k];
+  h->g.Lxh = lattice[0] / 2;
+  h->g.Vh = (int)(V / 2);
+  h->g.Ls = Ls;
+  h->g.N5 = h->g.Vh * Ls;
+  h->Ls = Ls;
+  h->M5 = M5;
+  h->m = m;
+  h->alpha = alpha;
+  h->b.assign(b, b + Ls);
+  h->c.assign(c, c + Ls);
+  dwf_default_options(&h->opt);
+  if (opt) h->opt = *opt;
+  if (h->opt.bc_t != 1 && h->opt.bc_t != -1) {
+    delete h;
+    return fail(nullptr, DWF_ERR_INVALID_ARG, "bc_t must be +1 or -1");
+  }
+  if (!valid_prec(h->opt.precision_inner) || (h->opt.rb_parity != 0 && h->opt.rb_parity != 1)) {
+    delete h;
+    return fail(nullptr, DWF_ERR_INVALID_ARG, "bad precision_inner or rb_parity");
+  }
+  h->g.bc_t = h->opt.bc_t;
+  cudaGetDevice(&h->device);
+  MatSet* ms;
+  int rc = build_matset(h, alpha, m, &ms);
+  if (!rc) rc = build_matset(h, 1.0, 1.0, &ms);
+  if (rc) {
+    g_create_error = h->err;
+    dwf_destroy(h);
+    return rc;
+  }
+  for (int p = 0; p < 3; p++) {
+    const int prec = p == 0 ? P64 : (p == 1 ? P32 : P16);
+    if (cudaMalloc(&h->gauge[p], gauge_bytes(h->g, prec)) != cudaSuccess) {
+      cudaGetLastError();
+      dwf_destroy(h);
+      return fail(nullptr, DWF_ERR_OOM, "gauge allocation failed");
+    }
+  }
+  *out = h;
+  return DWF_OK;
+}
+
+int dwf_destroy(dwf_handle h) {
+  if (!h) return DWF_OK;
+  for (void* p : h->allocs) cudaFree(p);
+  for (auto& kv : h->ws) cudaFree(kv.second);
+  for (int p = 0; p < 3; p++) cudaFree(h->gauge[p]);
+  if (h->scal) {
+    cudaFree(h->scal);
+    cudaFree(h->partial);
+    cudaFree(h->counter);
+    cudaFreeHost(h->pinned);
+  }
+  delete h;
+  return DWF_OK;
+}
+
+const char* dwf_last_error(dwf_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int dwf_field_bytes(dwf_handle h, int prec, size_t* bytes) {
+  if (!h || !bytes || !valid_prec(prec)) return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  *bytes = field_bytes(h->g, prec);
+  return DWF_OK;
+}
+
+int dwf_load_gauge(dwf_handle h, const double* U, int is_device, dwf_stream s) {
+  if (!h || !U) return fail(h, DWF_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  const size_t bytes = (size_t)h->g.Vh * 2 * 4 * 9 * 16;
+  const double* src = U;
+  if (!is_device) {
+    void* tmp;
+    int rc = get_ws(h, "gauge_in", bytes, &tmp);
+    if (rc) return rc;
+    CUCHK(h, cudaMemcpyAsync(tmp, U, bytes, cudaMemcpyHostToDevice, st));
+    src = reinterpret_cast<const double*>(tmp);
+  }
+  CUCHK(h, launch_gauge_convert(h->g, src, h->gauge[0], h->gauge[1], h->gauge[2], st));
+  h->gauge_loaded = true;
+  return DWF_OK;
+}
+
+int dwf_pack_half(dwf_handle h, void* dst, const double* src, int prec, int nrhs, dwf_stream s) {
+  if (!h || !dst || !src || !valid_prec(prec) || nrhs < 1)
+    return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  CUCHK(h, launch_pack_half(h->g, prec, dst, src, nrhs, reinterpret_cast<cudaStream_t>(s)));
+  return DWF_OK;
+}
+
+int dwf_unpack_half(dwf_handle h, double* dst, const void* src, int prec, int nrhs, dwf_stream s) {
+  if (!h || !dst || !src || !valid_prec(prec) || nrhs < 1)
+    return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  CUCHK(h, launch_unpack_half(h->g, prec, dst, src, nrhs, reinterpret_cast<cudaStream_t>(s)));
+  return DWF_OK;
+}
+
+int dwf_apply_Dbb(dwf_handle h, void* out, const void* in, int prec, int nrhs, dwf_stream s) {
+  if (!h || !out || !in || !valid_prec(prec) || nrhs < 1 || out == in)
+    return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  if (!h->gauge_loaded) return fail(h, DWF_ERR_STATE, "gauge field not loaded");
+  MatSet* ms;
+  int rc = build_matset(h, h->alpha, h->m, &ms);
+  if (rc) return rc;
+  void* tmp;
+  if ((rc = get_ws(h, "apply_red_" + std::to_string(prec), field_bytes(h->g, prec) * nrhs, &tmp))) return rc;
+  return apply_dbb(h, *ms, prec, out, in, tmp, nrhs, nullptr, reinterpret_cast<cudaStream_t>(s));
+}
+
+int dwf_apply_Dbb_dag(dwf_handle h, void* out, const void* in, int prec, int nrhs, dwf_stream s) {
+  if (!h || !out || !in || !valid_prec(prec) || nrhs < 1 || out == in)
+    return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  if (!h->gauge_loaded) return fail(h, DWF_ERR_STATE, "gauge field not loaded");
+  MatSet* ms;
+  int rc = build_matset(h, h->alpha, h->m, &ms);
+  if (rc) return rc;
+  void *tr, *tb;
+  const size_t fb = field_bytes(h->g, prec) * nrhs;
+  if ((rc = get_ws(h, "apply_red_" + std::to_string(prec), fb, &tr))) return rc;
+  if ((rc = get_ws(h, "apply_blk_" + std::to_string(prec), fb, &tb))) return rc;
+  return apply_dbb_dag(h, *ms, prec, out, in, tr, tb, nrhs, nullptr, reinterpret_cast<cudaStream_t>(s));
+}
+
+int dwf_apply_dalpha(dwf_handle h, double* out_full, const double* in_full, double alpha, double m,
+                     dwf_stream s) {
+  if (!h || !out_full || !in_full) return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  if (!h->gauge_loaded) return fail(h, DWF_ERR_STATE, "gauge field not loaded");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  MatSet* ms;
+  int rc = build_matset(h, alpha, m, &ms);
+  if (rc) return rc;
+  const size_t f64 = field_bytes(h->g, P64);
+  void *i0, *i1, *o0, *o1;
+  if ((rc = get_ws(h, "da_i0", f64, &i0)) || (rc = get_ws(h, "da_i1", f64, &i1)) ||
+      (rc = get_ws(h, "da_o0", f64, &o0)) || (rc = get_ws(h, "da_o1", f64, &o1)))
+    return rc;
+  CUCHK(h, launch_split_full(h->g, i0, i1, in_full, st));
+  void* outs[2] = {o0, o1};
+  const void* ins[2] = {i0, i1};
+  if ((rc = apply_dalpha_halves(h, *ms, outs, ins, st))) return rc;
+  CUCHK(h, launch_merge_full(h->g, out_full, o0, o1, st));
+  return DWF_OK;
+}
+
+int dwf_solve_normal(dwf_handle h, double* x_half, const double* phi_half, dwf_stats* stats,
+                     dwf_stream s) {
+  (void)h;
+  (void)x_half;
+  (void)phi_half;
+  (void)stats;
+  (void)s;
+  return fail(h, DWF_ERR_STATE, "not implemented");
+}
+
+int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* sol5d, int nrhs,
+                   const double* alphas, dwf_stats* stats, dwf_stream s) {
+  if (!h || !src4d || !prop4d || nrhs < 1) return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  if (!h->gauge_loaded) return fail(h, DWF_ERR_STATE, "gauge field not loaded");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  const Geom& g = h->g;
+  const size_t src_bytes = (size_t)g.Vh * 2 * 12 * 16;
+  const bool host = !is_device_ptr(src4d);
+  int rc;
+  if ((rc = ensure_reduce(h, nrhs))) return rc;
+  int prec;
+  double delta;
+  bool restart;
+  solver_params(h, &prec, &delta, &restart);
+  SolveWork W;
+  if ((rc = alloc_solve_work(h, prec, W))) return rc;
+  const size_t f64 = field_bytes(g, P64);
+  void *pb[2], *rhs[2], *psi_r, *src_d, *prop_d, *tmp5[2];
+  if ((rc = get_ws(h, "pb0", f64, &pb[0])) || (rc = get_ws(h, "pb1", f64, &pb[1])) ||
+      (rc = get_ws(h, "rhs0", f64, &rhs[0])) || (rc = get_ws(h, "rhs1", f64, &rhs[1])) ||
+      (rc = get_ws(h, "psi_r", f64, &psi_r)) || (rc = get_ws(h, "t5a", f64, &tmp5[0])) ||
+      (rc = get_ws(h, "t5b", f64, &tmp5[1])))
+    return rc;
+  if (host) {
+    if ((rc = get_ws(h, "src_d", src_bytes, &src_d)) || (rc = get_ws(h, "prop_d", src_bytes, &prop_d)))
+      return rc;
+  }
+  MatSet* rhs_set;
+  if ((rc = build_matset(h, 1.0, 1.0, &rhs_set))) return rc;
+  const int black = h->opt.rb_parity, red = 1 - black;
+  int result = DWF_OK;
+  for (int k = 0; k < nrhs; k++) {
+    auto t0 = std::chrono::steady_clock::now();
+    const double alpha = alphas ? alphas[k] : h->alpha;
+    MatSet* ms;
+    if ((rc = build_matset(h, alpha, h->m, &ms))) return rc;
+    const double* src_k = src4d + (size_t)k * src_bytes / 8;
+    if (host) {
+      CUCHK(h, cudaMemcpyAsync(src_d, src_k, src_bytes, cudaMemcpyHostToDevice, st));
+      src_k = reinterpret_cast<const double*>(src_d);
+    }
+    // rhs = D_1(1) P b
+    CUCHK(h, launch_source_pb(g, pb[0], pb[1], src_k, st));
+    const void* pbc[2] = {pb[0], pb[1]};
+    if ((rc = apply_dalpha_halves(h, *rhs_set, rhs, pbc, st))) return rc;
+    // r'_b = I^-1 rhs_b + 1/2 I^-1 H_br (K rhs_r)
+    LocalLaunch Lk{};
+    Lk.prec = P64;
+    Lk.out = W.t64r;
+    Lk.in = rhs[red];
+    Lk.stride = f64;
+    Lk.nrhs = 1;
+    Lk.m = ms->ptr(P64, ms->mat_off(MatSet::K));
+    Lk.c = 1.0;
+    CUCHK(h, launch_local(g, Lk, st));
+    HopLaunch Hs = base_hop(h, P64, black, 1, f64);
+    Hs.out = W.b_hi;
+    Hs.v = W.t64r;
+    Hs.w = rhs[black];
+    Hs.post = ms->ptr(P64, ms->mat_off(MatSet::IINV));
+    Hs.loc = LOC_DENSE;
+    Hs.locm = ms->ptr(P64, ms->mat_off(MatSet::IINV));
+    Hs.c_hop = 0.5;
+    Hs.c_loc = 1.0;
+    CUCHK(h, launch_hop(g, Hs, st));
+    dwf_stats sk{};
+    rc = cgnr_solve(h, *ms, prec, h->opt.rel_tol, h->opt.maxiter, delta, restart, W, &sk, st);
+    if (rc && rc != DWF_ERR_NOT_CONVERGED) return rc;
+    if (rc) result = rc;
+    // psi_r = I^-1 rhs_r + 1/2 I^-1 H_rb (B psi_b)
+    HopLaunch Hr = base_hop(h, P64, red, 1, f64);
+    Hr.out = psi_r;
+    Hr.v = W.x_hi;
+    Hr.w = rhs[red];
+    Hr.pre = PRE_B;
+    Hr.pre_diag = ms->ptr(P64, ms->bdiag_off());
+    Hr.pre_off = ms->ptr(P64, ms->boff_off());
+    Hr.post = ms->ptr(P64, ms->mat_off(MatSet::IINV));
+    Hr.loc = LOC_DENSE;
+    Hr.locm = ms->ptr(P64, ms->mat_off(MatSet::IINV));
+    Hr.c_hop = 0.5;
+    Hr.c_loc = 1.0;
+    CUCHK(h, launch_hop(g, Hr, st));
+    void* psi[2];
+    psi[black] = W.x_hi;
+    psi[red] = psi_r;
+    double* prop_k = prop4d + (size_t)k * src_bytes / 8;
+    CUCHK(h, launch_extract_z1(g, host ? reinterpret_cast<double*>(prop_d) : prop_k, psi[0], psi[1], st));
+    if (host) CUCHK(h, cudaMemcpyAsync(prop_k, prop_d, src_bytes, cudaMemcpyDeviceToHost, st));
+    if (sol5d) CUCHK(h, launch_merge_full(g, sol5d + (size_t)k * g.N5 * 2 * 24, psi[0], psi[1], st));
+    // full 5D residual |rhs - D_alpha psi| / |rhs|
+    const void* psic[2] = {psi[0], psi[1]};
+    if ((rc = apply_dalpha_halves(h, *ms, tmp5, psic, st))) return rc;
+    Reduce r0 = make_reduce(h, 0, S_T0), r1 = make_reduce(h, 1, S_T1);
+    Reduce n0 = make_reduce(h, 2, S_T2), n1 = make_reduce(h, 3, S_ZZ0);
+    CUCHK(h, launch_sub64_norm(g, tmp5[0], rhs[0], tmp5[0], 1, f64, &r0, st));
+    CUCHK(h, launch_sub64_norm(g, tmp5[1], rhs[1], tmp5[1], 1, f64, &r1, st));
+    CUCHK(h, launch_norm(g, P64, rhs[0], 1, f64, &n0, st));
+    CUCHK(h, launch_norm(g, P64, rhs[1], 1, f64, &n1, st));
+    if ((rc = sync_read(h, 1, st))) return rc;
+    sk.true_resid_5d = std::sqrt((h->pinned[S_T0] + h->pinned[S_T1]) / (h->pinned[S_T2] + h->pinned[S_ZZ0]));
+    sk.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) stats[k] = sk;
+  }
+  return result;
+}
+
+int dwf_force(dwf_handle h, double* dSdU, const double* phi_half, const double* X_half,
+              int projected, dwf_stream s) {
+  (void)dSdU;
+  (void)phi_half;
+  (void)X_half;
+  (void)projected;
+  (void)s;
+  return fail(h, DWF_ERR_STATE, "not implemented");
+}
+
+}  // extern "C"

@@ -1,0 +1,494 @@
+// dwf_blas.cu -- layout conversions, sources, propagator extraction and the
+// fused BLAS-1 kernels of the CG on the normal equations (sm_103a).
+#include "dwf_fields.cuh"
+
+namespace dwf {
+
+namespace {
+
+constexpr int kBlasThreads = 256;
+
+__device__ void reduce_block(double v, const Reduce& red, int rhs, int nblocks, int bid) {
+  __shared__ double wsum[32];
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? wsum[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    double* part = red.partial + (size_t)rhs * red.partial_stride;
+    unsigned int ticket = 0;
+    if (lane == 0) {
+      part[bid] = v;
+      __threadfence();
+      ticket = atomicAdd(red.counter + rhs, 1u);
+    }
+    ticket = __shfl_sync(0xffffffffu, ticket, 0);
+    if (ticket == (unsigned)(nblocks - 1)) {
+      __threadfence();
+      double acc = 0.0;
+      for (int b = lane; b < nblocks; b += 32) acc += *((volatile double*)(part + b));
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        red.result[(size_t)rhs * red.result_stride] = acc;
+        red.counter[rhs] = 0u;
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ double sqd(const Spinor<T>& a) {
+  T r = 0;
+#pragma unroll
+  for (int k = 0; k < 12; k++) r += a.c[k].re * a.c[k].re + a.c[k].im * a.c[k].im;
+  return (double)r;
+}
+
+template <typename TD, typename TS>
+__device__ __forceinline__ void cvt(Spinor<TD>& d, const Spinor<TS>& s) {
+#pragma unroll
+  for (int k = 0; k < 12; k++) d.c[k] = cmake((TD)s.c[k].re, (TD)s.c[k].im);
+}
+
+// ---- conversions --------------------------------------------------------------
+
+template <class SP>
+__global__ void pack_half_kernel(const Geom g, void* dst, const double* src, size_t stride,
+                                 int nrhs) {
+  using T = typename SP::T;
+  const size_t total = (size_t)g.N5 * nrhs;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / g.N5);
+    const int q = (int)(i % g.N5);
+    const int s = q / g.Vh, h = q % g.Vh;  // canonical order [s][h]
+    const double2* in = reinterpret_cast<const double2*>(src) + ((size_t)r * g.N5 + q) * 12;
+    Spinor<T> a;
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      double2 v = in[k];
+      a.c[k] = cmake((T)v.x, (T)v.y);
+    }
+    SP::store(reinterpret_cast<char*>(dst) + r * stride, h * g.Ls + s, g.N5, a);
+  }
+}
+
+template <class SP>
+__global__ void unpack_half_kernel(const Geom g, double* dst, const void* src, size_t stride,
+                                   int nrhs) {
+  using T = typename SP::T;
+  const size_t total = (size_t)g.N5 * nrhs;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / g.N5);
+    const int q = (int)(i % g.N5);
+    const int s = q / g.Vh, h = q % g.Vh;
+    Spinor<T> a;
+    SP::load(reinterpret_cast<const char*>(src) + r * stride, h * g.Ls + s, g.N5, a);
+    double2* out = reinterpret_cast<double2*>(dst) + ((size_t)r * g.N5 + q) * 12;
+#pragma unroll
+    for (int k = 0; k < 12; k++) out[k] = make_double2((double)a.c[k].re, (double)a.c[k].im);
+  }
+}
+
+__device__ __forceinline__ void lex_coords(const Geom& g, int i, int& x, int& y, int& z, int& t) {
+  x = i % g.L[0];
+  int r = i / g.L[0];
+  y = r % g.L[1];
+  r /= g.L[1];
+  z = r % g.L[2];
+  t = r / g.L[2];
+}
+
+// full canonical [Ls][V][4][3] <-> FP64 internal halves
+__global__ void split_full_kernel(const Geom g, void* p0, void* p1, const double* full, int to_full) {
+  const size_t V = (size_t)g.Vh * 2;
+  const size_t total = V * g.Ls;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int s = (int)(i / V);
+    const int site = (int)(i % V);
+    int x, y, z, t;
+    lex_coords(g, site, x, y, z, t);
+    const int par = (x + y + z + t) & 1;
+    const int h = site >> 1;
+    void* half = par ? p1 : p0;
+    double2* cf = reinterpret_cast<double2*>(const_cast<double*>(full)) + i * 12;
+    Spinor<double> a;
+    if (!to_full) {
+#pragma unroll
+      for (int k = 0; k < 12; k++) a.c[k] = cmake(cf[k].x, cf[k].y);
+      Store64::store(half, h * g.Ls + s, g.N5, a);
+    } else {
+      Store64::load(half, h * g.Ls + s, g.N5, a);
+#pragma unroll
+      for (int k = 0; k < 12; k++) cf[k] = make_double2(a.c[k].re, a.c[k].im);
+    }
+  }
+}
+
+__global__ void gauge_convert_kernel(const Geom g, const double* U, double2* g64, float4* g32,
+                                     uint4* g16) {
+  const size_t V = (size_t)g.Vh * 2;
+  const size_t total = V * 4;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int site = (int)(i / 4), mu = (int)(i % 4);
+    int x, y, z, t;
+    lex_coords(g, site, x, y, z, t);
+    const int par = (x + y + z + t) & 1;
+    const size_t slot = (size_t)par * g.Vh + (site >> 1);
+    const double2* u = reinterpret_cast<const double2*>(U) + i * 9;
+    double2 v[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) v[k] = u[k];
+    double2* d64 = g64 + (slot * 4 + mu) * 9;
+#pragma unroll
+    for (int k = 0; k < 9; k++) d64[k] = v[k];
+    float f[20];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      f[2 * k] = (float)v[k].x;
+      f[2 * k + 1] = (float)v[k].y;
+    }
+    f[18] = 0.f;
+    f[19] = 0.f;
+    float4* d32 = g32 + (slot * 4 + mu) * 5;
+#pragma unroll
+    for (int k = 0; k < 5; k++) d32[k] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+    uint32_t w[12];
+#pragma unroll
+    for (int k = 0; k < 9; k++)
+      w[k] = (uint32_t)__half_as_ushort(__float2half_rn((float)v[k].x)) |
+             ((uint32_t)__half_as_ushort(__float2half_rn((float)v[k].y)) << 16);
+    w[9] = w[10] = w[11] = 0u;
+    uint4* d16 = g16 + (slot * 4 + mu) * 3;
+#pragma unroll
+    for (int k = 0; k < 3; k++) d16[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+  }
+}
+
+// (Pb)_1 = P_- b_1 (spins 2,3), (Pb)_Ls = P_+ b_1 (spins 0,1); zero elsewhere.
+__global__ void source_pb_kernel(const Geom g, void* p0, void* p1, const double* src) {
+  const size_t V = (size_t)g.Vh * 2;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, z, t;
+    lex_coords(g, (int)i, x, y, z, t);
+    const int par = (x + y + z + t) & 1;
+    const int h = (int)(i >> 1);
+    void* half = par ? p1 : p0;
+    const double2* b = reinterpret_cast<const double2*>(src) + i * 12;
+    for (int s = 0; s < g.Ls; s++) {
+      Spinor<double> a;
+#pragma unroll
+      for (int k = 0; k < 12; k++) a.c[k] = cmake(0.0, 0.0);
+      if (s == 0) {
+#pragma unroll
+        for (int k = 6; k < 12; k++) a.c[k] = cmake(b[k].x, b[k].y);
+      }
+      if (s == g.Ls - 1) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) a.c[k] = cmake(b[k].x, b[k].y);
+      }
+      Store64::store(half, h * g.Ls + s, g.N5, a);
+    }
+  }
+}
+
+// z_1 = P_- psi_1 + P_+ psi_Ls
+__global__ void extract_z1_kernel(const Geom g, double* prop, const void* p0, const void* p1) {
+  const size_t V = (size_t)g.Vh * 2;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < V;
+       i += (size_t)gridDim.x * blockDim.x) {
+    int x, y, z, t;
+    lex_coords(g, (int)i, x, y, z, t);
+    const int par = (x + y + z + t) & 1;
+    const int h = (int)(i >> 1);
+    const void* half = par ? p1 : p0;
+    Spinor<double> a, b;
+    Store64::load(half, h * g.Ls + 0, g.N5, a);
+    Store64::load(half, h * g.Ls + g.Ls - 1, g.N5, b);
+    double2* o = reinterpret_cast<double2*>(prop) + i * 12;
+#pragma unroll
+    for (int k = 0; k < 6; k++) o[k] = make_double2(b.c[k].re, b.c[k].im);
+#pragma unroll
+    for (int k = 6; k < 12; k++) o[k] = make_double2(a.c[k].re, a.c[k].im);
+  }
+}
+
+// ---- BLAS-1 -------------------------------------------------------------------
+
+template <class SP>
+__global__ void __launch_bounds__(kBlasThreads) xr_update_kernel(
+    const Geom g, void* x, void* r, const void* p, const void* w, const double* num,
+    const double* den, int sstride, size_t stride, Reduce red) {
+  using T = typename SP::T;
+  const int rhs = blockIdx.y;
+  const size_t off = rhs * stride;
+  const T a = (T)(num[rhs * sstride] / den[rhs * sstride]);
+  double acc = 0.0;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
+    Spinor<T> xv, rv, pv, wv;
+    SP::load(reinterpret_cast<const char*>(x) + off, n, g.N5, xv);
+    SP::load(reinterpret_cast<const char*>(r) + off, n, g.N5, rv);
+    SP::load(reinterpret_cast<const char*>(p) + off, n, g.N5, pv);
+    SP::load(reinterpret_cast<const char*>(w) + off, n, g.N5, wv);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      xv.c[k] = cmake(fma(a, pv.c[k].re, xv.c[k].re), fma(a, pv.c[k].im, xv.c[k].im));
+      rv.c[k] = cmake(fma(-a, wv.c[k].re, rv.c[k].re), fma(-a, wv.c[k].im, rv.c[k].im));
+    }
+    SP::store(reinterpret_cast<char*>(x) + off, n, g.N5, xv);
+    SP::store(reinterpret_cast<char*>(r) + off, n, g.N5, rv);
+    acc += sqd(rv);
+  }
+  reduce_block(acc, red, rhs, gridDim.x, blockIdx.x);
+}
+
+template <class SP>
+__global__ void __launch_bounds__(kBlasThreads) p_update_kernel(
+    const Geom g, void* p, const void* z, const double* num, const double* den, int sstride,
+    size_t stride) {
+  using T = typename SP::T;
+  const int rhs = blockIdx.y;
+  const size_t off = rhs * stride;
+  const T beta = (T)(num[rhs * sstride] / den[rhs * sstride]);
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
+    Spinor<T> pv, zv;
+    SP::load(reinterpret_cast<const char*>(p) + off, n, g.N5, pv);
+    SP::load(reinterpret_cast<const char*>(z) + off, n, g.N5, zv);
+#pragma unroll
+    for (int k = 0; k < 12; k++)
+      pv.c[k] = cmake(fma(beta, pv.c[k].re, zv.c[k].re), fma(beta, pv.c[k].im, zv.c[k].im));
+    SP::store(reinterpret_cast<char*>(p) + off, n, g.N5, pv);
+  }
+}
+
+template <class SPD, class SPS>
+__global__ void __launch_bounds__(kBlasThreads) convert_kernel(
+    const Geom g, void* dst, const void* src, size_t sd, size_t ss, Reduce red, int do_norm) {
+  using TD = typename SPD::T;
+  using TS = typename SPS::T;
+  const int rhs = blockIdx.y;
+  double acc = 0.0;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
+    Spinor<TS> a;
+    SPS::load(reinterpret_cast<const char*>(src) + rhs * ss, n, g.N5, a);
+    Spinor<TD> b;
+    cvt(b, a);
+    SPD::store(reinterpret_cast<char*>(dst) + rhs * sd, n, g.N5, b);
+    if (do_norm) {
+      Spinor<TD> c;
+      SPD::load(reinterpret_cast<const char*>(dst) + rhs * sd, n, g.N5, c);
+      acc += sqd(c);
+    }
+  }
+  if (do_norm) reduce_block(acc, red, rhs, gridDim.x, blockIdx.x);
+}
+
+template <class SPS>
+__global__ void __launch_bounds__(kBlasThreads) accumulate64_kernel(
+    const Geom g, void* x64, void* src, int zero_src, size_t sd, size_t ss) {
+  using TS = typename SPS::T;
+  const int rhs = blockIdx.y;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
+    Spinor<TS> a;
+    SPS::load(reinterpret_cast<const char*>(src) + rhs * ss, n, g.N5, a);
+    Spinor<double> x;
+    Store64::load(reinterpret_cast<const char*>(x64) + rhs * sd, n, g.N5, x);
+#pragma unroll
+    for (int k = 0; k < 12; k++) x.c[k] = cmake(x.c[k].re + (double)a.c[k].re, x.c[k].im + (double)a.c[k].im);
+    Store64::store(reinterpret_cast<char*>(x64) + rhs * sd, n, g.N5, x);
+    if (zero_src) {
+      Spinor<TS> zz;
+#pragma unroll
+      for (int k = 0; k < 12; k++) zz.c[k] = cmake<TS>(0, 0);
+      SPS::store(reinterpret_cast<char*>(src) + rhs * ss, n, g.N5, zz);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlasThreads) sub64_norm_kernel(
+    const Geom g, void* out, const void* a, const void* b, size_t stride, Reduce red) {
+  const int rhs = blockIdx.y;
+  const size_t off = rhs * stride;
+  double acc = 0.0;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
+    Spinor<double> x, y;
+    Store64::load(reinterpret_cast<const char*>(a) + off, n, g.N5, x);
+    Store64::load(reinterpret_cast<const char*>(b) + off, n, g.N5, y);
+#pragma unroll
+    for (int k = 0; k < 12; k++) x.c[k] = x.c[k] - y.c[k];
+    Store64::store(reinterpret_cast<char*>(out) + off, n, g.N5, x);
+    acc += sqd(x);
+  }
+  reduce_block(acc, red, rhs, gridDim.x, blockIdx.x);
+}
+
+template <class SP>
+__global__ void __launch_bounds__(kBlasThreads) norm_kernel(const Geom g, const void* x,
+                                                             size_t stride, Reduce red) {
+  using T = typename SP::T;
+  const int rhs = blockIdx.y;
+  double acc = 0.0;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
+    Spinor<T> a;
+    SP::load(reinterpret_cast<const char*>(x) + rhs * stride, n, g.N5, a);
+    acc += sqd(a);
+  }
+  reduce_block(acc, red, rhs, gridDim.x, blockIdx.x);
+}
+
+int elementwise_blocks(size_t n) {
+  size_t b = (n + kBlasThreads - 1) / kBlasThreads;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+int blas_grid_blocks(const Geom& g) { return elementwise_blocks((size_t)g.N5); }
+
+size_t field_bytes(const Geom& g, int prec) {
+  size_t b = 0;
+  switch (prec) {
+    case P64: b = (size_t)g.N5 * 192; break;
+    case P32: b = (size_t)g.N5 * 96; break;
+    case P16:
+    case PB16: b = (size_t)g.N5 * 52; break;
+    default: return 0;
+  }
+  return (b + 255) / 256 * 256;
+}
+
+size_t gauge_bytes(const Geom& g, int prec) {
+  const size_t links = (size_t)g.Vh * 2 * 4;
+  switch (prec) {
+    case P64: return links * 144;
+    case P32: return links * 80;
+    default: return links * 48;
+  }
+}
+
+#define DWF_PREC_SWITCH(prec, SP, ...)                 \
+  switch (prec) {                                      \
+    case P64: { using SP = Store64; __VA_ARGS__; } break;        \
+    case P32: { using SP = Store32; __VA_ARGS__; } break;        \
+    case P16: { using SP = Store16<false>; __VA_ARGS__; } break; \
+    case PB16: { using SP = Store16<true>; __VA_ARGS__; } break; \
+    default: return cudaErrorInvalidValue;             \
+  }
+
+cudaError_t launch_pack_half(const Geom& g, int prec, void* dst, const double* src, int nrhs,
+                             cudaStream_t s) {
+  const size_t stride = field_bytes(g, prec);
+  const int blocks = elementwise_blocks((size_t)g.N5 * nrhs);
+  DWF_PREC_SWITCH(prec, SP, pack_half_kernel<SP><<<blocks, kBlasThreads, 0, s>>>(g, dst, src, stride, nrhs));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_half(const Geom& g, int prec, double* dst, const void* src, int nrhs,
+                               cudaStream_t s) {
+  const size_t stride = field_bytes(g, prec);
+  const int blocks = elementwise_blocks((size_t)g.N5 * nrhs);
+  DWF_PREC_SWITCH(prec, SP, unpack_half_kernel<SP><<<blocks, kBlasThreads, 0, s>>>(g, dst, src, stride, nrhs));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_full(const Geom& g, void* p0, void* p1, const double* full, cudaStream_t s) {
+  split_full_kernel<<<elementwise_blocks((size_t)g.N5 * 2), kBlasThreads, 0, s>>>(g, p0, p1, full, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_full(const Geom& g, double* full, const void* p0, const void* p1,
+                              cudaStream_t s) {
+  split_full_kernel<<<elementwise_blocks((size_t)g.N5 * 2), kBlasThreads, 0, s>>>(
+      g, const_cast<void*>(p0), const_cast<void*>(p1), full, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauge_convert(const Geom& g, const double* U, void* g64, void* g32, void* g16,
+                                 cudaStream_t s) {
+  gauge_convert_kernel<<<elementwise_blocks((size_t)g.Vh * 8), kBlasThreads, 0, s>>>(
+      g, U, reinterpret_cast<double2*>(g64), reinterpret_cast<float4*>(g32),
+      reinterpret_cast<uint4*>(g16));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_source_pb(const Geom& g, void* p0, void* p1, const double* src, cudaStream_t s) {
+  source_pb_kernel<<<elementwise_blocks((size_t)g.Vh * 2), kBlasThreads, 0, s>>>(g, p0, p1, src);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extract_z1(const Geom& g, double* prop, const void* p0, const void* p1,
+                              cudaStream_t s) {
+  extract_z1_kernel<<<elementwise_blocks((size_t)g.Vh * 2), kBlasThreads, 0, s>>>(g, prop, p0, p1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xr_update(const Geom& g, int prec, void* x, void* r, const void* p, const void* w,
+                             const double* num, const double* den, int sstride, int nrhs,
+                             size_t stride, const Reduce* red, cudaStream_t s) {
+  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  DWF_PREC_SWITCH(prec, SP, xr_update_kernel<SP><<<grid, kBlasThreads, 0, s>>>(g, x, r, p, w, num, den, sstride, stride, *red));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_p_update(const Geom& g, int prec, void* p, const void* z, const double* num,
+                            const double* den, int sstride, int nrhs, size_t stride,
+                            cudaStream_t s) {
+  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  DWF_PREC_SWITCH(prec, SP, p_update_kernel<SP><<<grid, kBlasThreads, 0, s>>>(g, p, z, num, den, sstride, stride));
+  return cudaGetLastError();
+}
+
+template <class SPD>
+cudaError_t convert_from(const Geom& g, void* dst, int prec_s, const void* src, int nrhs, size_t sd,
+                         size_t ss, const Reduce* red, cudaStream_t s) {
+  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  Reduce r{};
+  if (red) r = *red;
+  const int dn = red != nullptr;
+  DWF_PREC_SWITCH(prec_s, SPS, convert_kernel<SPD, SPS><<<grid, kBlasThreads, 0, s>>>(g, dst, src, sd, ss, r, dn));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const Geom& g, int prec_d, void* dst, int prec_s, const void* src,
+                           int nrhs, size_t sd, size_t ss, const Reduce* red, cudaStream_t s) {
+  switch (prec_d) {
+    case P64: return convert_from<Store64>(g, dst, prec_s, src, nrhs, sd, ss, red, s);
+    case P32: return convert_from<Store32>(g, dst, prec_s, src, nrhs, sd, ss, red, s);
+    case P16: return convert_from<Store16<false>>(g, dst, prec_s, src, nrhs, sd, ss, red, s);
+    case PB16: return convert_from<Store16<true>>(g, dst, prec_s, src, nrhs, sd, ss, red, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_accumulate64(const Geom& g, void* x64, int prec_s, void* src, int zero_src,
+                                int nrhs, size_t sd, size_t ss, cudaStream_t s) {
+  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  DWF_PREC_SWITCH(prec_s, SPS, accumulate64_kernel<SPS><<<grid, kBlasThreads, 0, s>>>(g, x64, src, zero_src, sd, ss));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub64_norm(const Geom& g, void* out, const void* a, const void* b, int nrhs,
+                              size_t stride, const Reduce* red, cudaStream_t s) {
+  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  sub64_norm_kernel<<<grid, kBlasThreads, 0, s>>>(g, out, a, b, stride, *red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm(const Geom& g, int prec, const void* x, int nrhs, size_t stride,
+                        const Reduce* red, cudaStream_t s) {
+  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  DWF_PREC_SWITCH(prec, SP, norm_kernel<SP><<<grid, kBlasThreads, 0, s>>>(g, x, stride, *red));
+  return cudaGetLastError();
+}
+
+}  // namespace dwf

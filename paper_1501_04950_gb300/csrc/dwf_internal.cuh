@@ -1,0 +1,154 @@
+// dwf_internal.cuh -- layouts, geometry and kernel launchers shared by the
+// translation units of libdwf (GB300, sm_103a).
+//
+// Internal half-field layout (5th dimension innermost, s fastest):
+//   5D index n = h * Ls + s, h the half-lattice site index of the canonical
+//   layout; N5 = Vh * Ls.  Components are stored chunk-major so that a warp
+//   reading one chunk of 32 consecutive n touches 512 contiguous bytes:
+//     FP64  double2 [12][N5]   (one complex per chunk, spin-major: spin*3+colour)
+//     FP32  float4  [6][N5]    (two complex per chunk)
+//     FP16/BF16  uint4 [3][N5] (four complex per chunk) + float scale[N5]
+//   Spins 0, 1 are the P_+ chirality (gamma5 = +1), spins 2, 3 are P_-.
+//
+// Gauge layout per parity p (sites of parity p, half index h):
+//   FP64  double2 [Vh][4 mu][9]          (row-major 3x3)
+//   FP32  float4  [Vh][4 mu][5]          (18 floats + 2 pad, row-major)
+//   FP16  uint4   [Vh][4 mu][3]          (9 (re,im) half pairs + 3 pad words)
+// The parity-1 copy follows the parity-0 copy in one allocation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace dwf {
+
+constexpr int kMaxLs = 32;
+
+struct Geom {
+  int L[4];      // Lx, Ly, Lz, Lt
+  int Lxh;       // Lx / 2
+  int Vh;        // sites per parity
+  int Ls;
+  int N5;        // Vh * Ls
+  int bc_t;      // +1 periodic, -1 antiperiodic in t
+};
+
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
+
+// Reduction target of a fused |.|^2.  Block b of right-hand side r writes
+// partial[r * partial_stride + b]; the last block of r to finish (ticket from
+// counter[r]) adds the partials in block order and stores result[r * result_stride].
+struct Reduce {
+  double* partial;
+  unsigned int* counter;
+  double* result;
+  int partial_stride;
+  int result_stride;
+};
+
+// ---- the generic hopping pass -------------------------------------------------
+//   acc(x,s)  = sum_mu [ (1-g_mu) U_mu(x) v'(x+mu,s) + (1+g_mu) U_mu(x-mu)^+ v'(x-mu,s) ]
+//   v'        = B v (cyclic bidiagonal per chirality), gamma5 v, or v
+//   out(x,s)  = c_hop * G * post(acc) + c_loc * loc(w)
+//   post, loc: dense (s, s') contraction per chirality, or identity / none;
+//   G = gamma5 if g5out.  Optional fused |out|^2 per right-hand side.
+enum PreOp { PRE_NONE = 0, PRE_B = 1, PRE_G5 = 2 };
+enum LocOp { LOC_NONE = 0, LOC_ID = 1, LOC_DENSE = 2 };
+
+struct HopLaunch {
+  int prec;                 // Prec of out, v, w
+  int p;                    // output parity
+  void* out;
+  const void* v;            // parity 1-p input
+  const void* w;            // parity p input of the local term
+  size_t stride;            // bytes between right-hand sides (all three fields)
+  int nrhs;
+  const void* gauge;        // gauge field of the precision (both parities)
+  size_t gauge_parity_bytes;
+  int pre;
+  const void* pre_diag;     // [2][Ls] compute type
+  const void* pre_off;      // [2][Ls]
+  const void* post;         // [2][Ls][Ls] compute type, row-major, or nullptr
+  int loc;
+  const void* locm;         // [2][Ls][Ls] for LOC_DENSE
+  double c_hop, c_loc;
+  int g5out;
+  const Reduce* red;        // nullptr: no norm
+  int block_sites;          // 4D sites per CTA (0: default)
+};
+cudaError_t launch_hop(const Geom& g, const HopLaunch& a, cudaStream_t s);
+int hop_grid_blocks(const Geom& g, int prec, int block_sites);
+
+// ---- site-local dense contraction: out = c * M (gamma5^g5in in) ---------------
+struct LocalLaunch {
+  int prec;
+  void* out;
+  const void* in;
+  size_t stride;
+  int nrhs;
+  const void* m;            // [2][Ls][Ls] compute type
+  double c;
+  int g5in;
+  const Reduce* red;
+};
+cudaError_t launch_local(const Geom& g, const LocalLaunch& a, cudaStream_t s);
+
+// ---- conversions ---------------------------------------------------------------
+size_t field_bytes(const Geom& g, int prec);
+size_t gauge_bytes(const Geom& g, int prec);  // both parities
+cudaError_t launch_pack_half(const Geom& g, int prec, void* dst, const double* src, int nrhs,
+                             cudaStream_t s);
+cudaError_t launch_unpack_half(const Geom& g, int prec, double* dst, const void* src, int nrhs,
+                               cudaStream_t s);
+// Canonical full 5D field <-> two internal FP64 half-fields (parity 0, parity 1).
+cudaError_t launch_split_full(const Geom& g, void* par0, void* par1, const double* full,
+                              cudaStream_t s);
+cudaError_t launch_merge_full(const Geom& g, double* full, const void* par0, const void* par1,
+                              cudaStream_t s);
+cudaError_t launch_gauge_convert(const Geom& g, const double* U, void* g64, void* g32,
+                                 void* g16, cudaStream_t s);
+// (P b) for b = (b_1, 0, ..., 0) on both parities, FP64 internal (App. A Eq. eqP):
+// (Pb)_1 = P_- b_1, (Pb)_Ls = P_+ b_1.
+cudaError_t launch_source_pb(const Geom& g, void* par0, void* par1, const double* src4d,
+                             cudaStream_t s);
+// z_1 = P_- psi_1 + P_+ psi_Ls (P^-1 of Eq. eqP) -> canonical 4D field.
+cudaError_t launch_extract_z1(const Geom& g, double* prop4d, const void* par0, const void* par1,
+                              cudaStream_t s);
+
+// ---- BLAS-1 (thread per 5D site; n_rhs right-hand sides back to back) ---------
+// x += a p; r -= a w; |r|^2 -> red.  a = num[r*sstride] / den[r*sstride].
+cudaError_t launch_xr_update(const Geom& g, int prec, void* x, void* r, const void* p,
+                             const void* w, const double* num, const double* den, int sstride,
+                             int nrhs, size_t stride, const Reduce* red, cudaStream_t s);
+// p = z + beta p, beta = num / den.
+cudaError_t launch_p_update(const Geom& g, int prec, void* p, const void* z, const double* num,
+                            const double* den, int sstride, int nrhs, size_t stride,
+                            cudaStream_t s);
+// dst (prec_d) = src (prec_s), optional |dst|^2 (of the converted values).
+cudaError_t launch_convert(const Geom& g, int prec_d, void* dst, int prec_s, const void* src,
+                           int nrhs, size_t stride_d, size_t stride_s, const Reduce* red,
+                           cudaStream_t s);
+// x64 += src (prec_s); then src = 0 if zero_src.
+cudaError_t launch_accumulate64(const Geom& g, void* x64, int prec_s, void* src, int zero_src,
+                                int nrhs, size_t stride_d, size_t stride_s, cudaStream_t s);
+// out = a - b (FP64), |out|^2 -> red.
+cudaError_t launch_sub64_norm(const Geom& g, void* out, const void* a, const void* b, int nrhs,
+                              size_t stride, const Reduce* red, cudaStream_t s);
+// |x|^2 -> red.
+cudaError_t launch_norm(const Geom& g, int prec, const void* x, int nrhs, size_t stride,
+                        const Reduce* red, cudaStream_t s);
+// Number of blocks the BLAS-1 launches use (partial buffers must hold this many).
+int blas_grid_blocks(const Geom& g);
+
+// ---- force (dwf_force.cu) -------------------------------------------------------
+// G_mu(x) += coef * sum_s [ eta(x)^+ (1-g_mu) . w(x+mu) + w(x)^+ ... ] outer products
+// (see the kernel for the exact form), eta on parity pe, w on parity 1-pe.
+cudaError_t launch_force_outer(const Geom& g, double* G, const void* eta, const void* w,
+                               int pe, double coef, cudaStream_t s);
+cudaError_t launch_force_project(const Geom& g, double* F, const double* U, const double* G,
+                                 int projected, cudaStream_t s);
+
+}  // namespace dwf

@@ -1,0 +1,119 @@
+"""GPU parity of the D_bb / D_bb^+ / D_alpha applies against the FP64 oracle.
+
+Tolerances (max_x |diff(x)| / RMS_x |ref(x)| over 5D half-sites):
+  FP64  1e-12 (the required apply parity),
+  FP32  5e-6  (FP32 rounding of inputs, links and ~3e3 accumulations per site),
+  FP16  1e-2  (11-bit significands of inputs, links and the intermediate field),
+  BF16  5e-2  (8-bit significands).
+Lattices are chosen so that the last CTA is ragged (Vh not a multiple of the
+sites per CTA) and so that Ls ranges over 4 .. 16.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from synthetic import gaussian_half5d
+
+from gpu_common import make_case, site_norm_error
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 5e-6, 2: 1e-2, 3: 5e-2}
+CASES = [
+    ((4, 4, 4, 4), 8, "shamir"),
+    ((6, 4, 2, 4), 12, "varying"),
+    ((2, 2, 2, 6), 4, "mobius"),
+    ((4, 2, 6, 2), 16, "mobius"),
+]
+
+
+def _op(sysm, **kw):
+    from paper_1501_04950_gb300 import dwf
+    op = dwf.DWF(sysm.lattice, sysm.Ls, sysm.M5, sysm.m, sysm.alpha, sysm.b, sysm.c,
+                 bc_t=int(sysm.bc_t), rb_parity=sysm.black_parity, **kw)
+    op.load_gauge(torch.from_numpy(sysm.U).cuda())
+    return op
+
+
+def _apply(op, psi, prec, dag=False, nrhs=1):
+    x = op.new_field(prec, nrhs)
+    y = op.new_field(prec, nrhs)
+    op.pack_half(x, torch.from_numpy(np.ascontiguousarray(psi)).cuda(), prec, nrhs)
+    (op.apply_Dbb_dag if dag else op.apply_Dbb)(y, x, prec, nrhs)
+    out = torch.empty(psi.shape, dtype=torch.complex128, device="cuda")
+    op.unpack_half(out, y, prec, nrhs)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("L,Ls,coeff", CASES)
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_dbb_parity(L, Ls, coeff, prec):
+    sysm = make_case(L, Ls, coeff)
+    op = _op(sysm)
+    psi = gaussian_half5d(L, Ls, seed=2)
+    ref = sysm.dbb(psi)
+    err = site_norm_error(_apply(op, psi, prec), ref)
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("L,Ls,coeff", CASES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_dbb_dag_parity(L, Ls, coeff, prec):
+    sysm = make_case(L, Ls, coeff, alpha=0.75)
+    op = _op(sysm)
+    psi = gaussian_half5d(L, Ls, seed=3)
+    ref = sysm.dbb_dag(psi)
+    err = site_norm_error(_apply(op, psi, prec, dag=True), ref)
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("bc_t,black", [(-1, 0), (1, 1), (-1, 1)])
+def test_dbb_boundary_and_parity_options(bc_t, black):
+    sysm = make_case((4, 4, 2, 4), 6, "varying", bc_t=bc_t, black=black)
+    op = _op(sysm)
+    psi = gaussian_half5d(sysm.lattice, 6, seed=4)
+    assert site_norm_error(_apply(op, psi, 0), sysm.dbb(psi)) <= 1e-12
+    assert site_norm_error(_apply(op, psi, 0, dag=True), sysm.dbb_dag(psi)) <= 1e-12
+
+
+def test_multi_rhs_apply_equals_single():
+    sysm = make_case((4, 4, 4, 2), 8, "mobius")
+    op = _op(sysm)
+    psis = np.stack([gaussian_half5d(sysm.lattice, 8, seed=10 + k) for k in range(3)])
+    for prec in (0, 1):
+        got = _apply(op, psis, prec, nrhs=3)
+        for k in range(3):
+            one = _apply(op, psis[k], prec)
+            assert np.array_equal(got[k], one)
+            assert site_norm_error(got[k], sysm.dbb(psis[k])) <= TOL[prec]
+
+
+@pytest.mark.parametrize("alpha,m,bc_t", [(1.3, 0.07, 1), (1.0, 1.0, 1), (0.6, 0.02, -1)])
+def test_dalpha_full_parity(alpha, m, bc_t):
+    sysm = make_case((4, 2, 4, 4), 8, "varying", bc_t=bc_t)
+    from paper_1501_04950_gb300 import dwf
+    op = dwf.DWF(sysm.lattice, 8, sysm.M5, sysm.m, sysm.alpha, sysm.b, sysm.c, bc_t=bc_t)
+    op.load_gauge(torch.from_numpy(sysm.U).cuda())
+    rng = np.random.default_rng(5)
+    shp = (8,) + O.shape4(sysm.lattice) + (4, 3)
+    psi = rng.standard_normal(shp) + 1j * rng.standard_normal(shp)
+    out = torch.empty(shp, dtype=torch.complex128, device="cuda")
+    op.apply_dalpha(out, torch.from_numpy(psi).cuda(), alpha, m)
+    ref = O.dalpha(psi, sysm.U, sysm.M5, sysm.b, sysm.c, alpha, m, float(bc_t))
+    got = out.cpu().numpy()
+    assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-13
+
+
+def test_dbb_adjoint_identity_fp64():
+    """<u, D v> = <D^+ u, v> on the GPU path alone (a property at any size)."""
+    sysm = make_case((4, 4, 4, 4), 8, "mobius")
+    op = _op(sysm)
+    u = gaussian_half5d(sysm.lattice, 8, seed=6)
+    v = gaussian_half5d(sysm.lattice, 8, seed=7)
+    dv = _apply(op, v, 0)
+    du = _apply(op, u, 0, dag=True)
+    lhs = np.vdot(u.ravel(), dv.ravel())
+    rhs = np.vdot(du.ravel(), v.ravel())
+    assert abs(lhs - rhs) < 1e-13 * abs(lhs)
