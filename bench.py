@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the alpha-Mobius red-black domain-wall solve on GB300.
+
+Workload (named in the JSON line): 16^3x32 lattice, Ls = 16, Mobius b = 1.5,
+c = 0.5, M5 = -1.8, m = 0.01, alpha = 1.0 (--alpha), synthetic SU(3) links
+U = exp(i 0.5 H) (seed 0) and a Gaussian 4D source (seed 1).  One step is one
+complete propagator solve through the C ABI (dwf_cgne_solve): right-hand side
+D_1(1) P b, Schur source, CG on the normal equations of D_bb with FP32 inner
+applies and FP64 reliable updates to FP64 true residual 1e-10, reconstruction
+of the red half and extraction of z_1.
+
+value: D_bb-apply bytes per second over the whole timed solve, i.e.
+(D_bb + D_bb^+ applies) x algorithmic bytes per apply / wall time of the steps,
+with the two-pass byte model 120 w_s + 16 r w_g / Ls per 5D half-site
+(w_s, w_g bytes per real of spinor and gauge, r = 18 reals per link).
+roofline: the D_bb apply (hop pass A + pass B) timed with CUDA events on the
+solver's stream inside the timed region, against the measured HBM copy peak.
+cpu_baseline / --impl reference: the FP64 numpy oracle's D_bb apply on a
+bounded sample (8^3x16 sub-lattice, same parameters), with the FP64 byte model.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+LATTICE = (16, 16, 16, 32)
+LS = 16
+M5, MASS, B, C, EPS = -1.8, 0.01, 1.5, 0.5, 0.5
+SAMPLE_LATTICE = (8, 8, 8, 16)
+METRIC = "D_bb apply GB/s inside CGNE to true residual 1e-10 (16^3x32, Ls=16)"
+GAUGE_REALS = 18
+
+
+def bytes_per_site(ws, wg, Ls, r=GAUGE_REALS):
+    """Two-pass algorithmic bytes of one D_bb apply per 5D half-site."""
+    return 120 * ws + 16 * r * wg / Ls
+
+
+def workload_name(alpha):
+    return ("16^3x32 Ls=16 Mobius b=1.5 c=0.5 M5=-1.8 m=0.01 alpha=%g eps=0.5, "
+            "Gaussian source; mixed FP32/FP64 CGNE to 1e-10" % alpha)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for name in ["dwf_hop.cu", "dwf_fields.cuh", "dwf_internal.cuh"]:
+        with open(os.path.join(ROOT, "paper_1501_04950_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """dram bytes per D_bb apply from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "dbb_apply_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("kernel_hash") != kernel_hash():
+        return None
+    return t.get("dram_bytes_per_apply_full_size")
+
+
+class ClockSampler:
+    def __init__(self, index=0):
+        self.proc = None
+        self.index = index
+        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_apply_sample(reps):
+    """Time the FP64 oracle's D_bb apply on the sample lattice; returns (GB/s, seconds list)."""
+    import oracle as O
+    from synthetic import gauge_field, gaussian_half5d
+    U = gauge_field(SAMPLE_LATTICE, EPS, seed=0)
+    sysm = O.DWFSystem(SAMPLE_LATTICE, LS, M5, MASS, 1.0, np.full(LS, B), np.full(LS, C), U)
+    psi = gaussian_half5d(SAMPLE_LATTICE, LS, seed=2)
+    sysm.local_inverse()
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        sysm.dbb(psi)
+        times.append(time.perf_counter() - t0)
+    n5 = np.prod(SAMPLE_LATTICE) // 2 * LS
+    gbs = n5 * bytes_per_site(8, 8, LS) / statistics.median(times) / 1e9
+    return gbs, times
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    import oracle as O
+    from synthetic import gauge_field, gaussian_half5d
+    U = gauge_field(SAMPLE_LATTICE, EPS, seed=0)
+    sysm = O.DWFSystem(SAMPLE_LATTICE, LS, M5, MASS, args.alpha, np.full(LS, B), np.full(LS, C), U)
+    psi = gaussian_half5d(SAMPLE_LATTICE, LS, seed=2)
+    for _ in range(args.warmup):
+        sysm.dbb(psi)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sysm.dbb(psi)
+    dt = time.perf_counter() - t0
+    n5 = np.prod(SAMPLE_LATTICE) // 2 * LS
+    value = args.steps * n5 * bytes_per_site(8, 8, LS) / dt / 1e9
+    sample = "one FP64 D_bb apply per step on an 8^3x16, Ls=16 sub-lattice of the workload"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.alpha), "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_apply_only(args):
+    """Time D_bb and D_bb^+ applies alone (inner precision and FP64) with CUDA events."""
+    import torch
+    from paper_1501_04950_gb300 import dwf
+    from synthetic import gauge_field, gaussian_half5d
+    lat = tuple(int(v) for v in args.lattice.split(",")) if args.lattice else LATTICE
+    dev = torch.device("cuda", 0)
+    U = torch.from_numpy(gauge_field(lat, EPS, seed=0)).to(dev)
+    op = dwf.DWF(lat, LS, M5, MASS, args.alpha, np.full(LS, B), np.full(LS, C))
+    op.load_gauge(U)
+    psi = torch.from_numpy(gaussian_half5d(lat, LS, seed=2)).to(dev)
+    n5 = op.Vh * LS
+    res = {"lattice": list(lat), "Ls": LS}
+    for name, prec, ws, wg in [("fp32", dwf.FP32, 4, 4), ("fp16", dwf.FP16, 2, 2),
+                               ("bf16", dwf.BF16, 2, 2), ("fp64", dwf.FP64, 8, 8)]:
+        x = op.new_field(prec)
+        y = op.new_field(prec)
+        op.pack_half(x, psi, prec)
+        for fn, key in [(op.apply_Dbb, "dbb"), (op.apply_Dbb_dag, "dbb_dag")]:
+            reps = args.apply_only if prec != dwf.FP64 else max(1, args.apply_only // 10)
+            for _ in range(3):
+                fn(y, x, prec)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn(y, x, prec)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gbs = n5 * bytes_per_site(ws, wg, LS) / (ms / 1e3) / 1e9
+            res["%s_%s_us" % (key, name)] = round(ms * 1e3, 2)
+            res["%s_%s_gbs" % (key, name)] = round(gbs, 1)
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--alpha", type=float, default=1.0)
+    ap.add_argument("--inner", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--apply-only", type=int, default=0,
+                    help="run this many D_bb and D_bb^+ applies of the workload and report their "
+                         "CUDA-event times (the case the ncu captures use)")
+    ap.add_argument("--lattice", default=None, help="override Lx,Ly,Lz,Lt (apply-only mode)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if args.apply_only:
+        run_apply_only(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1501_04950_gb300 import dwf
+    from synthetic import gauge_field, gaussian_source4d
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    inner = {"fp32": dwf.FP32, "fp16": dwf.FP16, "bf16": dwf.BF16}[args.inner]
+    ws_bytes = {dwf.FP32: 4, dwf.FP16: 2, dwf.BF16: 2}[inner]
+    wg_bytes = 4 if inner == dwf.FP32 else 2
+
+    U = torch.from_numpy(gauge_field(LATTICE, EPS, seed=0)).to(dev)
+    src_h = torch.from_numpy(gaussian_source4d(LATTICE, seed=1 + rank)).pin_memory()
+    src = src_h.to(dev)
+    prop = torch.empty_like(src)
+    prop_h = torch.empty_like(src_h).pin_memory()
+    op = dwf.DWF(LATTICE, LS, M5, MASS, args.alpha, np.full(LS, B), np.full(LS, C),
+                 precision_inner=inner, profile=1)
+    op.load_gauge(U)
+    torch.cuda.synchronize()
+    n5 = op.Vh * LS
+    b_inner = n5 * bytes_per_site(ws_bytes, wg_bytes, LS)
+    b_fp64 = n5 * bytes_per_site(8, 8, LS)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def maxtime(t):
+        if world > 1:
+            x = torch.tensor([t], dtype=torch.float64, device=dev)
+            dist.all_reduce(x, op=dist.ReduceOp.MAX)
+            return float(x.item())
+        return t
+
+    for _ in range(args.warmup):
+        op.cgne_solve(src, prop)
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats += op.cgne_solve(src, prop)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    dt = maxtime(e0.elapsed_time(e1) / 1e3)
+    applies = sum(s["applies"] + s["applies_dag"] for s in stats)
+    applies64 = sum(s["applies_fp64"] for s in stats)
+    moved = applies * b_inner + applies64 * b_fp64
+    value = moved * world / dt / 1e9
+    apply_ms = sum(s["apply_ms"] for s in stats)
+    n_apply = sum(s["applies"] for s in stats)
+    achieved = n_apply * b_inner / (apply_ms / 1e3) / 1e9 if apply_ms > 0 else None
+    peak, peak_kind = peaks()
+    launches = sum(s["kernel_launches"] for s in stats)
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_stats = []
+    for _ in range(args.steps):
+        e2e_stats += op.cgne_solve(src_h, prop_h)
+    torch.cuda.synchronize()
+    dt_e2e = maxtime(time.perf_counter() - t0)
+    moved_e2e = sum((s["applies"] + s["applies_dag"]) * b_inner + s["applies_fp64"] * b_fp64
+                    for s in e2e_stats)
+    io_bytes = src_h.numel() * 16
+
+    fp64 = None
+    if not args.no_fp64_baseline:
+        op64 = dwf.DWF(LATTICE, LS, M5, MASS, args.alpha, np.full(LS, B), np.full(LS, C),
+                       solver=dwf.SOLVER_FP64)
+        op64.load_gauge(U)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s64 = op64.cgne_solve(src, prop)[0]
+        torch.cuda.synchronize()
+        fp64 = {"solve_ms": (time.perf_counter() - t0) * 1e3, "iterations": s64["iterations"],
+                "true_resid": s64["true_resid"]}
+        op64.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        gbs, times = oracle_apply_sample(3)
+        cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "median of 3 FP64 D_bb applies on an 8^3x16, Ls=16 sub-lattice "
+                         "(%.1f s each)" % statistics.median(times)}
+
+    if rank == 0:
+        solve_ms = dt / args.steps * 1e3
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": solve_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if inner == dwf.FP32 else args.inner, "data": "synthetic",
+            "config": {"workload": workload_name(args.alpha), "lattice": list(LATTICE), "Ls": LS,
+                       "inner": args.inner, "rel_tol": 1e-10, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set (gauge + ~8 half-fields, >1 GB) exceeds the 129 MB L2"},
+            "solve": {"time_to_1e-10_ms": solve_ms, "iterations": stats[0]["iterations"],
+                      "reliable_updates": stats[0]["restarts"], "true_resid": stats[0]["true_resid"],
+                      "true_resid_5d": stats[0]["true_resid_5d"],
+                      "fp64_plain": fp64,
+                      "speedup_vs_fp64": (fp64["solve_ms"] / solve_ms) if fp64 else None},
+            "roofline": {"kernel": "D_bb apply (hop pass A + pass B, FP32)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                         "peak_kind": peak_kind, "traffic": measured_traffic(),
+                         "bytes_per_apply": b_inner},
+            "cpu_baseline": cpu,
+            "e2e": {"value": moved_e2e * world / dt_e2e / 1e9, "unit": "GB/s",
+                    "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

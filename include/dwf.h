@@ -81,6 +81,7 @@ typedef struct {
   double reliable_delta; /* reliable update when |r| < delta * max|r| (default 0.1)  */
   int solver;            /* DWF_SOLVER_* (default DWF_SOLVER_RELIABLE)               */
   int check_every;       /* iterations between convergence polls (default 16)        */
+  int profile;           /* 1: time the inner applies with CUDA events (stats.apply_ms) */
 } dwf_options;
 
 typedef struct {
@@ -89,6 +90,12 @@ typedef struct {
   double true_resid;     /* FP64 |r'_b - D_bb x| / |r'_b| of the returned solution     */
   double true_resid_5d;  /* FP64 |rhs - D_alpha psi| / |rhs| of the full 5D solution    */
   double seconds;        /* wall time of the solve                                     */
+  int applies;           /* inner-precision D_bb applies                               */
+  int applies_dag;       /* inner-precision D_bb^+ applies                             */
+  int applies_fp64;      /* FP64 D_bb applies (true residuals)                          */
+  int kernel_launches;   /* CUDA kernels the solve launched                             */
+  double apply_ms;       /* device time of the inner D_bb applies (opt.profile = 1)     */
+  double apply_dag_ms;   /* device time of the inner D_bb^+ applies (opt.profile = 1)   */
 } dwf_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -147,6 +147,13 @@ struct dwf_ctx {
   int partial_stride = 0;
   int scal_rhs = 0;
   double* pinned = nullptr;        // host mirror of scal
+  long long launches = 0;          // kernels launched through this handle
+  // CUDA-event timing of the inner applies (opt.profile): pool and pending pairs
+  std::vector<cudaEvent_t> events;
+  std::vector<int> pending;        // (start index) of recorded pairs, kind in pending_kind
+  std::vector<int> pending_kind;
+  size_t next_event = 0;
+  double timed_ms[2] = {0, 0};
 };
 
 namespace {
@@ -159,6 +166,12 @@ int fail(dwf_ctx* h, int code, const std::string& msg) {
   else g_create_error = msg;
   return code;
 }
+
+#define KLAUNCH(h, expr)            \
+  do {                              \
+    (h)->launches++;                \
+    CUCHK(h, expr);                 \
+  } while (0)
 
 #define CUCHK(h, expr)                                                                       \
   do {                                                                                      \
@@ -303,7 +316,7 @@ int apply_dbb(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void* in,
   A.pre_diag = ms.ptr(prec, ms.bdiag_off());
   A.pre_off = ms.ptr(prec, ms.boff_off());
   A.post = ms.ptr(prec, ms.mat_off(MatSet::K));
-  CUCHK(h, launch_hop(h->g, A, s));
+  KLAUNCH(h, launch_hop(h->g, A, s));
   HopLaunch B = base_hop(h, prec, black, nrhs, st);
   B.out = out;
   B.v = tmp;
@@ -313,7 +326,7 @@ int apply_dbb(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void* in,
   B.c_hop = -0.25;
   B.c_loc = 1.0;
   B.red = norm;
-  CUCHK(h, launch_hop(h->g, B, s));
+  KLAUNCH(h, launch_hop(h->g, B, s));
   return DWF_OK;
 }
 
@@ -331,12 +344,12 @@ int apply_dbb_dag(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void*
   L.m = ms.ptr(prec, ms.mat_off(MatSet::IINVT));
   L.c = 1.0;
   L.g5in = 1;
-  CUCHK(h, launch_local(h->g, L, s));
+  KLAUNCH(h, launch_local(h->g, L, s));
   HopLaunch A = base_hop(h, prec, red, nrhs, st);
   A.out = tmp_red;
   A.v = tmp_blk;
   A.post = ms.ptr(prec, ms.mat_off(MatSet::KT));
-  CUCHK(h, launch_hop(h->g, A, s));
+  KLAUNCH(h, launch_hop(h->g, A, s));
   HopLaunch B = base_hop(h, prec, black, nrhs, st);
   B.out = out;
   B.v = tmp_red;
@@ -347,7 +360,7 @@ int apply_dbb_dag(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void*
   B.c_loc = 1.0;
   B.g5out = 1;
   B.red = norm;
-  CUCHK(h, launch_hop(h->g, B, s));
+  KLAUNCH(h, launch_hop(h->g, B, s));
   return DWF_OK;
 }
 
@@ -366,7 +379,7 @@ int apply_dalpha_halves(dwf_ctx* h, const MatSet& ms, void* out[2], const void* 
     L.locm = ms.ptr(P64, ms.mat_off(MatSet::IFULL));
     L.c_hop = -0.5;
     L.c_loc = 1.0;
-    CUCHK(h, launch_hop(h->g, L, s));
+    KLAUNCH(h, launch_hop(h->g, L, s));
   }
   return DWF_OK;
 }
@@ -404,9 +417,42 @@ int alloc_solve_work(dwf_ctx* h, int prec, SolveWork& W) {
   if ((rc = get_ws(h, "r" + sfx, fi, &W.r))) return rc;
   if ((rc = get_ws(h, "w" + sfx, fi, &W.w))) return rc;
   if ((rc = get_ws(h, "z" + sfx, fi, &W.z))) return rc;
-  if ((rc = get_ws(h, "xlo" + sfx, fi, &W.xlo))) return rc;
+  const int xprec = (prec == P16 || prec == PB16) ? P32 : prec;
+  if ((rc = get_ws(h, "xlo" + sfx, field_bytes(h->g, xprec), &W.xlo))) return rc;
   if ((rc = get_ws(h, "tb" + sfx, fi, &W.tb))) return rc;
   if ((rc = get_ws(h, "tr" + sfx, fi, &W.tr))) return rc;
+  return DWF_OK;
+}
+
+// Start/stop events around one apply (kind 0: D_bb, 1: D_bb^+) when profiling.
+int timer_mark(dwf_ctx* h, cudaStream_t s, bool start, int kind) {
+  if (!h->opt.profile) return DWF_OK;
+  if (h->next_event >= h->events.size()) {
+    cudaEvent_t e;
+    CUCHK(h, cudaEventCreate(&e));
+    h->events.push_back(e);
+  }
+  const int idx = (int)h->next_event++;
+  CUCHK(h, cudaEventRecord(h->events[idx], s));
+  if (start) {
+    h->pending.push_back(idx);
+    h->pending_kind.push_back(kind);
+  }
+  return DWF_OK;
+}
+
+// After a stream synchronisation: add the elapsed time of all recorded pairs.
+int timer_harvest(dwf_ctx* h) {
+  if (!h->opt.profile) return DWF_OK;
+  for (size_t k = 0; k < h->pending.size(); k++) {
+    float ms = 0.f;
+    const int i = h->pending[k];
+    CUCHK(h, cudaEventElapsedTime(&ms, h->events[i], h->events[i + 1]));
+    h->timed_ms[h->pending_kind[k]] += ms;
+  }
+  h->pending.clear();
+  h->pending_kind.clear();
+  h->next_event = 0;
   return DWF_OK;
 }
 
@@ -414,31 +460,62 @@ int alloc_solve_work(dwf_ctx* h, int prec, SolveWork& W) {
 // precision prec with FP64 reliable updates (residual replacement when |r|
 // drops below delta times its maximum since the last update) or, with
 // restart = true, FP64 defect correction (the inner CG restarts from p = z
-// after every update).  b_hi, x_hi: FP64 black fields; x_hi returned.
+// after every update).  b_hi, x_hi: FP64 black fields; x_hi returned.  The
+// inner solution increment x_lo is kept in FP32 when prec is 16-bit.
 int cgnr_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxiter, double delta,
                bool restart, SolveWork& W, dwf_stats* st, cudaStream_t s) {
-  const size_t f64 = field_bytes(h->g, P64), fi = field_bytes(h->g, prec);
+  const int xprec = (prec == P16 || prec == PB16) ? P32 : prec;
+  const size_t f64 = field_bytes(h->g, P64), fi = field_bytes(h->g, prec),
+               fx = field_bytes(h->g, xprec);
   Reduce red_ww = make_reduce(h, 0, S_WW), red_rr = make_reduce(h, 1, S_RR);
   Reduce red_zz[2] = {make_reduce(h, 2, S_ZZ0), make_reduce(h, 2, S_ZZ1)};
   Reduce red_hi = make_reduce(h, 3, S_RRHI), red_bb = make_reduce(h, 3, S_BB);
   int rc;
+  const long long launches0 = h->launches;
+  h->timed_ms[0] = h->timed_ms[1] = 0.0;
+  h->pending.clear();
+  h->pending_kind.clear();
+  h->next_event = 0;
+  int n_app = 0, n_dag = 0, n_64 = 0;
+  auto apply_inner = [&](void* out, const void* in, const Reduce* red) -> int {
+    int r;
+    if ((r = timer_mark(h, s, true, 0))) return r;
+    if ((r = apply_dbb(h, ms, prec, out, in, W.tr, 1, red, s))) return r;
+    n_app++;
+    return timer_mark(h, s, false, 0);
+  };
+  auto apply_inner_dag = [&](void* out, const void* in, const Reduce* red) -> int {
+    int r;
+    if ((r = timer_mark(h, s, true, 1))) return r;
+    if ((r = apply_dbb_dag(h, ms, prec, out, in, W.tr, W.tb, 1, red, s))) return r;
+    n_dag++;
+    return timer_mark(h, s, false, 1);
+  };
+  auto fill_stats = [&](int it, int restarts, double true_res) {
+    if (!st) return;
+    st->iterations = it;
+    st->restarts = restarts;
+    st->true_resid = true_res;
+    st->applies = n_app;
+    st->applies_dag = n_dag;
+    st->applies_fp64 = n_64;
+    st->apply_ms = h->timed_ms[0];
+    st->apply_dag_ms = h->timed_ms[1];
+    st->kernel_launches = (int)(h->launches - launches0);
+  };
   CUCHK(h, cudaMemsetAsync(W.x_hi, 0, f64, s));
-  CUCHK(h, cudaMemsetAsync(W.xlo, 0, fi, s));
-  CUCHK(h, launch_convert(h->g, P64, W.r_hi, P64, W.b_hi, 1, f64, f64, &red_bb, s));
-  CUCHK(h, launch_convert(h->g, prec, W.r, P64, W.b_hi, 1, fi, f64, nullptr, s));
+  CUCHK(h, cudaMemsetAsync(W.xlo, 0, fx, s));
+  KLAUNCH(h, launch_convert(h->g, P64, W.r_hi, P64, W.b_hi, 1, f64, f64, &red_bb, s));
+  KLAUNCH(h, launch_convert(h->g, prec, W.r, P64, W.b_hi, 1, fi, f64, nullptr, s));
   if ((rc = sync_read(h, 1, s))) return rc;
   const double bb = h->pinned[S_BB];
   if (!(bb > 0.0)) {
-    if (st) {
-      st->iterations = 0;
-      st->restarts = 0;
-      st->true_resid = 0.0;
-    }
+    fill_stats(0, 0, 0.0);
     return bb == 0.0 ? DWF_OK : fail(h, DWF_ERR_BREAKDOWN, "source norm is not finite");
   }
   const double bnorm = std::sqrt(bb);
   int cur = 0;
-  if ((rc = apply_dbb_dag(h, ms, prec, W.z, W.r, W.tr, W.tb, 1, &red_zz[cur], s))) return rc;
+  if ((rc = apply_inner_dag(W.z, W.r, &red_zz[cur]))) return rc;
   CUCHK(h, cudaMemcpyAsync(W.p, W.z, fi, cudaMemcpyDeviceToDevice, s));
   double rmax = bnorm;
   int it = 0, restarts = 0;
@@ -446,22 +523,27 @@ int cgnr_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxiter, 
   bool converged = false;
   const int check = std::max(1, h->opt.check_every);
   while (it < maxiter) {
-    if ((rc = apply_dbb(h, ms, prec, W.w, W.p, W.tr, 1, &red_ww, s))) return rc;
-    CUCHK(h, launch_xr_update(h->g, prec, W.xlo, W.r, W.p, W.w, h->scal + (cur ? S_ZZ1 : S_ZZ0),
-                              h->scal + S_WW, kScal, 1, fi, &red_rr, s));
+    if ((rc = apply_inner(W.w, W.p, &red_ww))) return rc;
+    KLAUNCH(h, launch_xr_update(h->g, prec, xprec, W.xlo, W.r, W.p, W.w,
+                                h->scal + (cur ? S_ZZ1 : S_ZZ0), h->scal + S_WW, kScal, 1, fx, fi,
+                                &red_rr, s));
     it++;
     if (it % check == 0 || it >= maxiter) {
       if ((rc = sync_read(h, 1, s))) return rc;
+      if ((rc = timer_harvest(h))) return rc;
       const double rr = h->pinned[S_RR], ww = h->pinned[S_WW];
-      if (!std::isfinite(rr) || !std::isfinite(ww) || !(ww > 0.0))
+      if (!std::isfinite(rr) || !std::isfinite(ww) || !(ww > 0.0)) {
+        fill_stats(it, restarts, true_res);
         return fail(h, DWF_ERR_BREAKDOWN, "CG breakdown (|Dp|^2 <= 0 or not finite)");
+      }
       const double rn = std::sqrt(rr);
       if (rn < delta * rmax || rn <= tol * bnorm || it >= maxiter) {
         // reliable update: x_hi += x_lo, r = b - D x_hi in FP64
-        CUCHK(h, launch_accumulate64(h->g, W.x_hi, prec, W.xlo, 1, 1, f64, fi, s));
+        KLAUNCH(h, launch_accumulate64(h->g, W.x_hi, xprec, W.xlo, 1, 1, f64, fx, s));
         if ((rc = apply_dbb(h, ms, P64, W.t64, W.x_hi, W.t64r, 1, nullptr, s))) return rc;
-        CUCHK(h, launch_sub64_norm(h->g, W.r_hi, W.b_hi, W.t64, 1, f64, &red_hi, s));
-        CUCHK(h, launch_convert(h->g, prec, W.r, P64, W.r_hi, 1, fi, f64, nullptr, s));
+        n_64++;
+        KLAUNCH(h, launch_sub64_norm(h->g, W.r_hi, W.b_hi, W.t64, 1, f64, &red_hi, s));
+        KLAUNCH(h, launch_convert(h->g, prec, W.r, P64, W.r_hi, 1, fi, f64, nullptr, s));
         if ((rc = sync_read(h, 1, s))) return rc;
         true_res = std::sqrt(h->pinned[S_RRHI]) / bnorm;
         rmax = std::sqrt(h->pinned[S_RRHI]);
@@ -473,23 +555,20 @@ int cgnr_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxiter, 
         if (it >= maxiter) break;
         if (restart) {
           cur = 0;
-          if ((rc = apply_dbb_dag(h, ms, prec, W.z, W.r, W.tr, W.tb, 1, &red_zz[cur], s))) return rc;
+          if ((rc = apply_inner_dag(W.z, W.r, &red_zz[cur]))) return rc;
           CUCHK(h, cudaMemcpyAsync(W.p, W.z, fi, cudaMemcpyDeviceToDevice, s));
           continue;
         }
       }
     }
     const int nxt = 1 - cur;
-    if ((rc = apply_dbb_dag(h, ms, prec, W.z, W.r, W.tr, W.tb, 1, &red_zz[nxt], s))) return rc;
-    CUCHK(h, launch_p_update(h->g, prec, W.p, W.z, h->scal + (nxt ? S_ZZ1 : S_ZZ0),
-                             h->scal + (cur ? S_ZZ1 : S_ZZ0), kScal, 1, fi, s));
+    if ((rc = apply_inner_dag(W.z, W.r, &red_zz[nxt]))) return rc;
+    KLAUNCH(h, launch_p_update(h->g, prec, W.p, W.z, h->scal + (nxt ? S_ZZ1 : S_ZZ0),
+                               h->scal + (cur ? S_ZZ1 : S_ZZ0), kScal, 1, fi, s));
     cur = nxt;
   }
-  if (st) {
-    st->iterations = it;
-    st->restarts = restarts;
-    st->true_resid = true_res;
-  }
+  if ((rc = timer_harvest(h))) return rc;
+  fill_stats(it, restarts, true_res);
   if (!converged) return fail(h, DWF_ERR_NOT_CONVERGED, "CG did not reach the tolerance within maxiter");
   return DWF_OK;
 }
@@ -521,6 +600,7 @@ int dwf_default_options(dwf_options* opt) {
   opt->reliable_delta = 0.1;
   opt->solver = DWF_SOLVER_RELIABLE;
   opt->check_every = 16;
+  opt->profile = 0;
   return DWF_OK;
 }
 
@@ -584,6 +664,7 @@ int dwf_destroy(dwf_handle h) {
   for (void* p : h->allocs) cudaFree(p);
   for (auto& kv : h->ws) cudaFree(kv.second);
   for (int p = 0; p < 3; p++) cudaFree(h->gauge[p]);
+  for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   if (h->scal) {
     cudaFree(h->scal);
     cudaFree(h->partial);
@@ -614,7 +695,7 @@ int dwf_load_gauge(dwf_handle h, const double* U, int is_device, dwf_stream s) {
     CUCHK(h, cudaMemcpyAsync(tmp, U, bytes, cudaMemcpyHostToDevice, st));
     src = reinterpret_cast<const double*>(tmp);
   }
-  CUCHK(h, launch_gauge_convert(h->g, src, h->gauge[0], h->gauge[1], h->gauge[2], st));
+  KLAUNCH(h, launch_gauge_convert(h->g, src, h->gauge[0], h->gauge[1], h->gauge[2], st));
   h->gauge_loaded = true;
   return DWF_OK;
 }
@@ -622,14 +703,14 @@ int dwf_load_gauge(dwf_handle h, const double* U, int is_device, dwf_stream s) {
 int dwf_pack_half(dwf_handle h, void* dst, const double* src, int prec, int nrhs, dwf_stream s) {
   if (!h || !dst || !src || !valid_prec(prec) || nrhs < 1)
     return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
-  CUCHK(h, launch_pack_half(h->g, prec, dst, src, nrhs, reinterpret_cast<cudaStream_t>(s)));
+  KLAUNCH(h, launch_pack_half(h->g, prec, dst, src, nrhs, reinterpret_cast<cudaStream_t>(s)));
   return DWF_OK;
 }
 
 int dwf_unpack_half(dwf_handle h, double* dst, const void* src, int prec, int nrhs, dwf_stream s) {
   if (!h || !dst || !src || !valid_prec(prec) || nrhs < 1)
     return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
-  CUCHK(h, launch_unpack_half(h->g, prec, dst, src, nrhs, reinterpret_cast<cudaStream_t>(s)));
+  KLAUNCH(h, launch_unpack_half(h->g, prec, dst, src, nrhs, reinterpret_cast<cudaStream_t>(s)));
   return DWF_OK;
 }
 
@@ -672,11 +753,11 @@ int dwf_apply_dalpha(dwf_handle h, double* out_full, const double* in_full, doub
   if ((rc = get_ws(h, "da_i0", f64, &i0)) || (rc = get_ws(h, "da_i1", f64, &i1)) ||
       (rc = get_ws(h, "da_o0", f64, &o0)) || (rc = get_ws(h, "da_o1", f64, &o1)))
     return rc;
-  CUCHK(h, launch_split_full(h->g, i0, i1, in_full, st));
+  KLAUNCH(h, launch_split_full(h->g, i0, i1, in_full, st));
   void* outs[2] = {o0, o1};
   const void* ins[2] = {i0, i1};
   if ((rc = apply_dalpha_halves(h, *ms, outs, ins, st))) return rc;
-  CUCHK(h, launch_merge_full(h->g, out_full, o0, o1, st));
+  KLAUNCH(h, launch_merge_full(h->g, out_full, o0, o1, st));
   return DWF_OK;
 }
 
@@ -732,7 +813,7 @@ int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* so
       src_k = reinterpret_cast<const double*>(src_d);
     }
     // rhs = D_1(1) P b
-    CUCHK(h, launch_source_pb(g, pb[0], pb[1], src_k, st));
+    KLAUNCH(h, launch_source_pb(g, pb[0], pb[1], src_k, st));
     const void* pbc[2] = {pb[0], pb[1]};
     if ((rc = apply_dalpha_halves(h, *rhs_set, rhs, pbc, st))) return rc;
     // r'_b = I^-1 rhs_b + 1/2 I^-1 H_br (K rhs_r)
@@ -744,7 +825,7 @@ int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* so
     Lk.nrhs = 1;
     Lk.m = ms->ptr(P64, ms->mat_off(MatSet::K));
     Lk.c = 1.0;
-    CUCHK(h, launch_local(g, Lk, st));
+    KLAUNCH(h, launch_local(g, Lk, st));
     HopLaunch Hs = base_hop(h, P64, black, 1, f64);
     Hs.out = W.b_hi;
     Hs.v = W.t64r;
@@ -754,8 +835,9 @@ int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* so
     Hs.locm = ms->ptr(P64, ms->mat_off(MatSet::IINV));
     Hs.c_hop = 0.5;
     Hs.c_loc = 1.0;
-    CUCHK(h, launch_hop(g, Hs, st));
+    KLAUNCH(h, launch_hop(g, Hs, st));
     dwf_stats sk{};
+    const long long launches_k0 = h->launches;
     rc = cgnr_solve(h, *ms, prec, h->opt.rel_tol, h->opt.maxiter, delta, restart, W, &sk, st);
     if (rc && rc != DWF_ERR_NOT_CONVERGED) return rc;
     if (rc) result = rc;
@@ -772,26 +854,27 @@ int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* so
     Hr.locm = ms->ptr(P64, ms->mat_off(MatSet::IINV));
     Hr.c_hop = 0.5;
     Hr.c_loc = 1.0;
-    CUCHK(h, launch_hop(g, Hr, st));
+    KLAUNCH(h, launch_hop(g, Hr, st));
     void* psi[2];
     psi[black] = W.x_hi;
     psi[red] = psi_r;
     double* prop_k = prop4d + (size_t)k * src_bytes / 8;
-    CUCHK(h, launch_extract_z1(g, host ? reinterpret_cast<double*>(prop_d) : prop_k, psi[0], psi[1], st));
+    KLAUNCH(h, launch_extract_z1(g, host ? reinterpret_cast<double*>(prop_d) : prop_k, psi[0], psi[1], st));
     if (host) CUCHK(h, cudaMemcpyAsync(prop_k, prop_d, src_bytes, cudaMemcpyDeviceToHost, st));
-    if (sol5d) CUCHK(h, launch_merge_full(g, sol5d + (size_t)k * g.N5 * 2 * 24, psi[0], psi[1], st));
+    if (sol5d) KLAUNCH(h, launch_merge_full(g, sol5d + (size_t)k * g.N5 * 2 * 24, psi[0], psi[1], st));
     // full 5D residual |rhs - D_alpha psi| / |rhs|
     const void* psic[2] = {psi[0], psi[1]};
     if ((rc = apply_dalpha_halves(h, *ms, tmp5, psic, st))) return rc;
     Reduce r0 = make_reduce(h, 0, S_T0), r1 = make_reduce(h, 1, S_T1);
     Reduce n0 = make_reduce(h, 2, S_T2), n1 = make_reduce(h, 3, S_ZZ0);
-    CUCHK(h, launch_sub64_norm(g, tmp5[0], rhs[0], tmp5[0], 1, f64, &r0, st));
-    CUCHK(h, launch_sub64_norm(g, tmp5[1], rhs[1], tmp5[1], 1, f64, &r1, st));
-    CUCHK(h, launch_norm(g, P64, rhs[0], 1, f64, &n0, st));
-    CUCHK(h, launch_norm(g, P64, rhs[1], 1, f64, &n1, st));
+    KLAUNCH(h, launch_sub64_norm(g, tmp5[0], rhs[0], tmp5[0], 1, f64, &r0, st));
+    KLAUNCH(h, launch_sub64_norm(g, tmp5[1], rhs[1], tmp5[1], 1, f64, &r1, st));
+    KLAUNCH(h, launch_norm(g, P64, rhs[0], 1, f64, &n0, st));
+    KLAUNCH(h, launch_norm(g, P64, rhs[1], 1, f64, &n1, st));
     if ((rc = sync_read(h, 1, st))) return rc;
     sk.true_resid_5d = std::sqrt((h->pinned[S_T0] + h->pinned[S_T1]) / (h->pinned[S_T2] + h->pinned[S_ZZ0]));
     sk.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    sk.kernel_launches = (int)(h->launches - launches_k0);
     if (stats) stats[k] = sk;
   }
   return result;

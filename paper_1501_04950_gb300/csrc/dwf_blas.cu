@@ -223,27 +223,31 @@ __global__ void extract_z1_kernel(const Geom g, double* prop, const void* p0, co
 
 // ---- BLAS-1 -------------------------------------------------------------------
 
-template <class SP>
+template <class SPX, class SP>
 __global__ void __launch_bounds__(kBlasThreads) xr_update_kernel(
     const Geom g, void* x, void* r, const void* p, const void* w, const double* num,
-    const double* den, int sstride, size_t stride, Reduce red) {
+    const double* den, int sstride, size_t stride_x, size_t stride, Reduce red) {
   using T = typename SP::T;
+  using TX = typename SPX::T;
   const int rhs = blockIdx.y;
-  const size_t off = rhs * stride;
-  const T a = (T)(num[rhs * sstride] / den[rhs * sstride]);
+  const size_t off = rhs * stride, offx = rhs * stride_x;
+  const double ad = num[rhs * sstride] / den[rhs * sstride];
+  const T a = (T)ad;
+  const TX ax = (TX)ad;
   double acc = 0.0;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
-    Spinor<T> xv, rv, pv, wv;
-    SP::load(reinterpret_cast<const char*>(x) + off, n, g.N5, xv);
+    Spinor<TX> xv;
+    Spinor<T> rv, pv, wv;
+    SPX::load(reinterpret_cast<const char*>(x) + offx, n, g.N5, xv);
     SP::load(reinterpret_cast<const char*>(r) + off, n, g.N5, rv);
     SP::load(reinterpret_cast<const char*>(p) + off, n, g.N5, pv);
     SP::load(reinterpret_cast<const char*>(w) + off, n, g.N5, wv);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      xv.c[k] = cmake(fma(a, pv.c[k].re, xv.c[k].re), fma(a, pv.c[k].im, xv.c[k].im));
+      xv.c[k] = cmake(fma(ax, (TX)pv.c[k].re, xv.c[k].re), fma(ax, (TX)pv.c[k].im, xv.c[k].im));
       rv.c[k] = cmake(fma(-a, wv.c[k].re, rv.c[k].re), fma(-a, wv.c[k].im, rv.c[k].im));
     }
-    SP::store(reinterpret_cast<char*>(x) + off, n, g.N5, xv);
+    SPX::store(reinterpret_cast<char*>(x) + offx, n, g.N5, xv);
     SP::store(reinterpret_cast<char*>(r) + off, n, g.N5, rv);
     acc += sqd(rv);
   }
@@ -432,11 +436,18 @@ cudaError_t launch_extract_z1(const Geom& g, double* prop, const void* p0, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_xr_update(const Geom& g, int prec, void* x, void* r, const void* p, const void* w,
-                             const double* num, const double* den, int sstride, int nrhs,
-                             size_t stride, const Reduce* red, cudaStream_t s) {
+cudaError_t launch_xr_update(const Geom& g, int prec, int xprec, void* x, void* r, const void* p,
+                             const void* w, const double* num, const double* den, int sstride,
+                             int nrhs, size_t stride_x, size_t stride, const Reduce* red,
+                             cudaStream_t s) {
   dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
-  DWF_PREC_SWITCH(prec, SP, xr_update_kernel<SP><<<grid, kBlasThreads, 0, s>>>(g, x, r, p, w, num, den, sstride, stride, *red));
+  if (xprec == prec) {
+    DWF_PREC_SWITCH(prec, SP, xr_update_kernel<SP, SP><<<grid, kBlasThreads, 0, s>>>(g, x, r, p, w, num, den, sstride, stride_x, stride, *red));
+  } else if (xprec == P32) {
+    DWF_PREC_SWITCH(prec, SP, xr_update_kernel<Store32, SP><<<grid, kBlasThreads, 0, s>>>(g, x, r, p, w, num, den, sstride, stride_x, stride, *red));
+  } else {
+    return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

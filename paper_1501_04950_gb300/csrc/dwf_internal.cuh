@@ -120,9 +120,11 @@ cudaError_t launch_extract_z1(const Geom& g, double* prop4d, const void* par0, c
 
 // ---- BLAS-1 (thread per 5D site; n_rhs right-hand sides back to back) ---------
 // x += a p; r -= a w; |r|^2 -> red.  a = num[r*sstride] / den[r*sstride].
-cudaError_t launch_xr_update(const Geom& g, int prec, void* x, void* r, const void* p,
+// x may be stored in a wider precision xprec (FP32 under FP16/BF16 r, p, w).
+cudaError_t launch_xr_update(const Geom& g, int prec, int xprec, void* x, void* r, const void* p,
                              const void* w, const double* num, const double* den, int sstride,
-                             int nrhs, size_t stride, const Reduce* red, cudaStream_t s);
+                             int nrhs, size_t stride_x, size_t stride, const Reduce* red,
+                             cudaStream_t s);
 // p = z + beta p, beta = num / den.
 cudaError_t launch_p_update(const Geom& g, int prec, void* p, const void* z, const double* num,
                             const double* den, int sstride, int nrhs, size_t stride,

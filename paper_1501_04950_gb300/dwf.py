@@ -29,13 +29,16 @@ class Options(ctypes.Structure):
     _fields_ = [("precision_inner", ctypes.c_int), ("rb_parity", ctypes.c_int),
                 ("bc_t", ctypes.c_int), ("rel_tol", ctypes.c_double), ("maxiter", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("solver", ctypes.c_int),
-                ("check_every", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("profile", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int),
                 ("true_resid", ctypes.c_double), ("true_resid_5d", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("applies", ctypes.c_int),
+                ("applies_dag", ctypes.c_int), ("applies_fp64", ctypes.c_int),
+                ("kernel_launches", ctypes.c_int), ("apply_ms", ctypes.c_double),
+                ("apply_dag_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -39,7 +39,7 @@ def test_config1_solve(solver, prec):
     zs = []
     for alpha in (1.0, 1.5):
         sysm = make_case(L, 8, "shamir", alpha=alpha, m=0.01, eps=0.3)
-        prop, sol, st = _solve(sysm, src, solver=solver, precision_inner=prec)
+        prop, sol, st = _solve(sysm, src, solver=solver, precision_inner=prec, maxiter=20000)
         assert st[0]["true_resid"] <= 1e-10, st
         ref = O.solve_propagator(sysm, src, tol=1e-12)
         err = np.abs(prop - ref["z1"]).max() / np.abs(ref["z1"]).max()
