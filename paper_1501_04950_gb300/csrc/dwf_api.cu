@@ -15,6 +15,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -22,6 +23,7 @@
 
 #include "../../include/dwf.h"
 #include "dwf_internal.cuh"
+#include "dwf_hop2.cuh"
 
 using namespace dwf;
 
@@ -41,7 +43,8 @@ struct MatSet {
   size_t mat_off(int which) const { return (size_t)which * 2 * Ls * Ls; }
   size_t bdiag_off() const { return (size_t)NMAT * 2 * Ls * Ls; }
   size_t boff_off() const { return bdiag_off() + 2 * (size_t)Ls; }
-  size_t count() const { return boff_off() + 2 * (size_t)Ls; }
+  size_t chain_off() const { return boff_off() + 2 * (size_t)Ls; }
+  size_t count() const { return chain_off() + (size_t)hop2::chain_block(Ls); }
   const void* ptr(int prec, size_t off) const {
     const int f = prec == P64 ? 0 : 1;
     const size_t es = f == 0 ? 8 : 4;
@@ -124,6 +127,64 @@ std::vector<double> transpose(const std::vector<double>& a, int n) {
   return t;
 }
 
+// Cyclic bidiagonal matrix (M y)_s = d_s y_s + o_s y_{(s + dir) mod Ls}.
+struct CycBidiag {
+  std::vector<double> d, o;
+  int dir;
+};
+
+CycBidiag extract_cb(const std::vector<double>& M, int Ls, int dir) {
+  CycBidiag r;
+  r.dir = dir;
+  r.d.resize(Ls);
+  r.o.resize(Ls);
+  for (int s = 0; s < Ls; s++) {
+    r.d[s] = M[(size_t)s * Ls + s];
+    r.o[s] = M[(size_t)s * Ls + (s + dir + Ls) % Ls];
+  }
+  return r;
+}
+
+// (M^T y)_s = d_s y_s + o_{s - dir} y_{s - dir}
+CycBidiag transpose_cb(const CycBidiag& m, int Ls) {
+  CycBidiag r;
+  r.dir = -m.dir;
+  r.d = m.d;
+  r.o.resize(Ls);
+  for (int s = 0; s < Ls; s++) r.o[s] = m.o[(s - m.dir + Ls) % Ls];
+  return r;
+}
+
+// Coefficients of the tuned kernels' recurrences in "lower" sweep order
+// (slice order reversed when dir = +1): multiply y_k = D_k v_k + O_k v_{k-1};
+// solve D_k y_k + O_k y_{k-1} = v_k by y_k = alpha_k + beta_k y_0.
+void chain_coeffs(const CycBidiag& m, int Ls, bool solve, double* out) {
+  const bool rev = m.dir == +1;
+  std::vector<double> D(Ls), O(Ls);
+  for (int k = 0; k < Ls; k++) {
+    const int s = rev ? Ls - 1 - k : k;
+    D[k] = m.d[s];
+    O[k] = m.o[s];
+  }
+  if (!solve) {
+    for (int k = 0; k < Ls; k++) {
+      out[k] = D[k];
+      out[Ls + k] = O[k];
+    }
+    return;
+  }
+  std::vector<double> beta(Ls);
+  beta[0] = 1.0;
+  for (int k = 1; k < Ls; k++) beta[k] = -(O[k] / D[k]) * beta[k - 1];
+  for (int k = 0; k < Ls; k++) {
+    out[k] = 1.0 / D[k];
+    out[Ls + k] = O[k] / D[k];
+    out[2 * Ls + k] = beta[k];
+  }
+  out[3 * Ls] = 1.0 / (D[0] + O[0] * beta[Ls - 1]);
+  out[3 * Ls + 1] = O[0];
+}
+
 }  // namespace
 
 struct dwf_ctx {
@@ -136,6 +197,9 @@ struct dwf_ctx {
   std::string err;
   std::map<std::pair<double, double>, MatSet> mats;
   void* gauge[3] = {nullptr, nullptr, nullptr};  // FP64, FP32, FP16
+  int* nbr = nullptr;                            // [2][Vh][8] neighbour table
+  int* dev_err = nullptr;                        // set by a kernel whose bounded wait gave up
+  int use_tma = 0;                               // DWF_TMA: bulk-copy staged tuned kernels
   bool gauge_loaded = false;
   std::vector<void*> allocs;
   // workspace
@@ -223,6 +287,20 @@ int build_matset(dwf_ctx* h, double alpha, double m, MatSet** out) {
       ms.host[ms.boff_off() + ch * Ls + s] = Ls == 1 ? 0.0 : Bm[ch][(size_t)s * Ls + col];
     }
   }
+  // recurrence coefficients of the tuned kernels
+  for (int ch = 0; ch < 2; ch++) {
+    std::vector<double> I(LL);
+    for (size_t k = 0; k < LL; k++) I[k] = (4.0 + h->M5) * Bm[ch][k] + Cm[ch][k];
+    const int dir = ch == 0 ? -1 : +1;
+    const CycBidiag Bc = extract_cb(Bm[ch], Ls, dir), Ic = extract_cb(I, Ls, dir);
+    const int cs = hop2::chain_stride(Ls);
+    double* base = ms.host.data() + ms.chain_off();
+    chain_coeffs(Bc, Ls, false, base + (hop2::OP_B * 2 + ch) * cs);
+    chain_coeffs(transpose_cb(Bc, Ls), Ls, false, base + (hop2::OP_BT * 2 + ch) * cs);
+    chain_coeffs(Ic, Ls, false, base + (hop2::OP_I * 2 + ch) * cs);
+    chain_coeffs(Ic, Ls, true, base + (hop2::OP_ISOLVE * 2 + ch) * cs);
+    chain_coeffs(transpose_cb(Ic, Ls), Ls, true, base + (hop2::OP_ITSOLVE * 2 + ch) * cs);
+  }
   std::vector<float> hf(ms.count());
   for (size_t k = 0; k < hf.size(); k++) hf[k] = (float)ms.host[k];
   CUCHK(h, cudaMalloc(&ms.dev[0], ms.count() * 8));
@@ -272,7 +350,7 @@ int ensure_reduce(dwf_ctx* h, int nrhs) {
   CUCHK(h, cudaMalloc(&h->counter, sizeof(unsigned int) * h->scal_rhs * 4));
   CUCHK(h, cudaMemset(h->counter, 0, sizeof(unsigned int) * h->scal_rhs * 4));
   CUCHK(h, cudaMemset(h->scal, 0, sizeof(double) * kScal * h->scal_rhs));
-  CUCHK(h, cudaMallocHost(&h->pinned, sizeof(double) * kScal * h->scal_rhs));
+  CUCHK(h, cudaMallocHost(&h->pinned, sizeof(double) * (kScal * h->scal_rhs + 1)));
   return DWF_OK;
 }
 
@@ -301,6 +379,9 @@ HopLaunch base_hop(dwf_ctx* h, int prec, int p, int nrhs, size_t stride) {
   L.gauge_parity_bytes = gauge_bytes(h->g, prec) / 2;
   L.c_hop = 1.0;
   L.c_loc = 0.0;
+  L.nbr = h->nbr;
+  L.err = h->dev_err;
+  L.use_tma = h->use_tma;
   return L;
 }
 
@@ -316,12 +397,16 @@ int apply_dbb(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void* in,
   A.pre_diag = ms.ptr(prec, ms.bdiag_off());
   A.pre_off = ms.ptr(prec, ms.boff_off());
   A.post = ms.ptr(prec, ms.mat_off(MatSet::K));
+  A.post_prog = hop2::PR_K;
+  A.chain = ms.ptr(prec, ms.chain_off());
   KLAUNCH(h, launch_hop(h->g, A, s));
   HopLaunch B = base_hop(h, prec, black, nrhs, st);
   B.out = out;
   B.v = tmp;
   B.w = in;
   B.post = ms.ptr(prec, ms.mat_off(MatSet::IINV));
+  B.post_prog = hop2::PR_IINV;
+  B.chain = ms.ptr(prec, ms.chain_off());
   B.loc = LOC_ID;
   B.c_hop = -0.25;
   B.c_loc = 1.0;
@@ -342,6 +427,8 @@ int apply_dbb_dag(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void*
   L.stride = st;
   L.nrhs = nrhs;
   L.m = ms.ptr(prec, ms.mat_off(MatSet::IINVT));
+  L.prog = hop2::PR_ITINV;
+  L.chain = ms.ptr(prec, ms.chain_off());
   L.c = 1.0;
   L.g5in = 1;
   KLAUNCH(h, launch_local(h->g, L, s));
@@ -349,12 +436,16 @@ int apply_dbb_dag(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void*
   A.out = tmp_red;
   A.v = tmp_blk;
   A.post = ms.ptr(prec, ms.mat_off(MatSet::KT));
+  A.post_prog = hop2::PR_KT;
+  A.chain = ms.ptr(prec, ms.chain_off());
   KLAUNCH(h, launch_hop(h->g, A, s));
   HopLaunch B = base_hop(h, prec, black, nrhs, st);
   B.out = out;
   B.v = tmp_red;
   B.w = in;
   B.post = ms.ptr(prec, ms.mat_off(MatSet::BT));
+  B.post_prog = hop2::PR_BT;
+  B.chain = ms.ptr(prec, ms.chain_off());
   B.loc = LOC_ID;
   B.c_hop = -0.25;
   B.c_loc = 1.0;
@@ -386,7 +477,15 @@ int apply_dalpha_halves(dwf_ctx* h, const MatSet& ms, void* out[2], const void* 
 
 int sync_read(dwf_ctx* h, int nrhs, cudaStream_t s) {
   CUCHK(h, cudaMemcpyAsync(h->pinned, h->scal, sizeof(double) * kScal * nrhs, cudaMemcpyDeviceToHost, s));
+  CUCHK(h, cudaMemcpyAsync(h->pinned + kScal * h->scal_rhs, h->dev_err, sizeof(int),
+                           cudaMemcpyDeviceToHost, s));
   CUCHK(h, cudaStreamSynchronize(s));
+  int flag;
+  std::memcpy(&flag, h->pinned + kScal * h->scal_rhs, sizeof(int));
+  if (flag) {
+    cudaMemsetAsync(h->dev_err, 0, sizeof(int), s);
+    return fail(h, DWF_ERR_TIMEOUT, "a kernel's bounded wait for its shared-memory copies gave up");
+  }
   return DWF_OK;
 }
 
@@ -638,6 +737,13 @@ int dwf_create(dwf_handle* out, const int lattice[4], int Ls, double M5, double 
     return fail(nullptr, DWF_ERR_INVALID_ARG, "bad precision_inner or rb_parity");
   }
   h->g.bc_t = h->opt.bc_t;
+  // DWF_GENERIC_KERNELS=1 selects the generic (any Ls, dense 5th-dimension)
+  // kernels instead of the tuned ones; used to cross-check the two paths.
+  g_disable_tuned = std::getenv("DWF_GENERIC_KERNELS") != nullptr;
+  // DWF_TMA=1 stages the neighbour blocks of the tuned FP32/16-bit kernels
+  // through shared memory with cp.async.bulk (measured slower than direct
+  // loads on the 16^3x32 workload; kept as an alternative staging strategy).
+  h->use_tma = std::getenv("DWF_TMA") != nullptr;
   cudaGetDevice(&h->device);
   MatSet* ms;
   int rc = build_matset(h, alpha, m, &ms);
@@ -646,6 +752,45 @@ int dwf_create(dwf_handle* out, const int lattice[4], int Ls, double M5, double 
     g_create_error = h->err;
     dwf_destroy(h);
     return rc;
+  }
+  {
+    // neighbour table: for each parity p and half index h the half indices of
+    // x+mu and x-mu (mu = x, y, z, t), bit 31 set where the hop crosses the t
+    // boundary with antiperiodic fermions
+    const int Lx = lattice[0], Ly = lattice[1], Lz = lattice[2], Lt = lattice[3];
+    const int Vh = h->g.Vh, Lxh = Lx / 2;
+    std::vector<int> tab((size_t)2 * Vh * 8);
+    for (int p = 0; p < 2; p++)
+      for (int hh = 0; hh < Vh; hh++) {
+        const int xh = hh % Lxh;
+        int r = hh / Lxh;
+        const int y = r % Ly;
+        r /= Ly;
+        const int z = r % Lz, t = r / Lz;
+        const int x = 2 * xh + ((y + z + t + p) & 1);
+        int* e = &tab[((size_t)p * Vh + hh) * 8];
+        const int c[4] = {x, y, z, t}, L4[4] = {Lx, Ly, Lz, Lt};
+        for (int mu = 0; mu < 4; mu++)
+          for (int d = 0; d < 2; d++) {
+            int cc[4] = {c[0], c[1], c[2], c[3]};
+            const int step = d == 0 ? 1 : -1;
+            cc[mu] += step;
+            bool cross = false;
+            if (cc[mu] < 0) { cc[mu] += L4[mu]; cross = true; }
+            if (cc[mu] >= L4[mu]) { cc[mu] -= L4[mu]; cross = true; }
+            int idx = (cc[0] >> 1) + Lxh * (cc[1] + Ly * (cc[2] + Lz * cc[3]));
+            if (mu == 3 && cross && h->opt.bc_t < 0) idx |= (int)0x80000000u;
+            e[mu * 2 + d] = idx;
+          }
+      }
+    if (cudaMalloc(&h->dev_err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(h->dev_err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&h->nbr, tab.size() * sizeof(int)) != cudaSuccess ||
+        cudaMemcpy(h->nbr, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      dwf_destroy(h);
+      return fail(nullptr, DWF_ERR_OOM, "neighbour table allocation failed");
+    }
   }
   for (int p = 0; p < 3; p++) {
     const int prec = p == 0 ? P64 : (p == 1 ? P32 : P16);
@@ -664,6 +809,8 @@ int dwf_destroy(dwf_handle h) {
   for (void* p : h->allocs) cudaFree(p);
   for (auto& kv : h->ws) cudaFree(kv.second);
   for (int p = 0; p < 3; p++) cudaFree(h->gauge[p]);
+  if (h->nbr) cudaFree(h->nbr);
+  if (h->dev_err) cudaFree(h->dev_err);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
   if (h->scal) {
     cudaFree(h->scal);

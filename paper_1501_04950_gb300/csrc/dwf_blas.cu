@@ -73,7 +73,7 @@ __global__ void pack_half_kernel(const Geom g, void* dst, const double* src, siz
       double2 v = in[k];
       a.c[k] = cmake((T)v.x, (T)v.y);
     }
-    SP::store(reinterpret_cast<char*>(dst) + r * stride, h * g.Ls + s, g.N5, a);
+    SP::store(reinterpret_cast<char*>(dst) + r * stride, site5(h, s, g.Ls), g.N5, a);
   }
 }
 
@@ -88,7 +88,7 @@ __global__ void unpack_half_kernel(const Geom g, double* dst, const void* src, s
     const int q = (int)(i % g.N5);
     const int s = q / g.Vh, h = q % g.Vh;
     Spinor<T> a;
-    SP::load(reinterpret_cast<const char*>(src) + r * stride, h * g.Ls + s, g.N5, a);
+    SP::load(reinterpret_cast<const char*>(src) + r * stride, site5(h, s, g.Ls), g.N5, a);
     double2* out = reinterpret_cast<double2*>(dst) + ((size_t)r * g.N5 + q) * 12;
 #pragma unroll
     for (int k = 0; k < 12; k++) out[k] = make_double2((double)a.c[k].re, (double)a.c[k].im);
@@ -122,9 +122,9 @@ __global__ void split_full_kernel(const Geom g, void* p0, void* p1, const double
     if (!to_full) {
 #pragma unroll
       for (int k = 0; k < 12; k++) a.c[k] = cmake(cf[k].x, cf[k].y);
-      Store64::store(half, h * g.Ls + s, g.N5, a);
+      Store64::store(half, site5(h, s, g.Ls), g.N5, a);
     } else {
-      Store64::load(half, h * g.Ls + s, g.N5, a);
+      Store64::load(half, site5(h, s, g.Ls), g.N5, a);
 #pragma unroll
       for (int k = 0; k < 12; k++) cf[k] = make_double2(a.c[k].re, a.c[k].im);
     }
@@ -195,7 +195,7 @@ __global__ void source_pb_kernel(const Geom g, void* p0, void* p1, const double*
 #pragma unroll
         for (int k = 0; k < 6; k++) a.c[k] = cmake(b[k].x, b[k].y);
       }
-      Store64::store(half, h * g.Ls + s, g.N5, a);
+      Store64::store(half, site5(h, s, g.Ls), g.N5, a);
     }
   }
 }
@@ -211,8 +211,8 @@ __global__ void extract_z1_kernel(const Geom g, double* prop, const void* p0, co
     const int h = (int)(i >> 1);
     const void* half = par ? p1 : p0;
     Spinor<double> a, b;
-    Store64::load(half, h * g.Ls + 0, g.N5, a);
-    Store64::load(half, h * g.Ls + g.Ls - 1, g.N5, b);
+    Store64::load(half, site5(h, 0, g.Ls), g.N5, a);
+    Store64::load(half, site5(h, g.Ls - 1, g.Ls), g.N5, b);
     double2* o = reinterpret_cast<double2*>(prop) + i * 12;
 #pragma unroll
     for (int k = 0; k < 6; k++) o[k] = make_double2(b.c[k].re, b.c[k].im);

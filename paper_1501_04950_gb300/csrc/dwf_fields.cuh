@@ -55,12 +55,22 @@ struct Link {
   cplx<T> u[9];  // row-major U[a][b] = u[3a+b]
 };
 
+// Position of slice s inside a 4D site's Ls consecutive 5D entries: even
+// slices first, then odd ones, so that threads owning the slice pairs
+// (2t, 2t+1) read and write contiguous memory for each of the two slices.
+__host__ __device__ __forceinline__ int slice_pos(int s, int Ls) {
+  return (s & 1) ? ((Ls + 1) >> 1) + (s >> 1) : (s >> 1);
+}
+__host__ __device__ __forceinline__ int site5(int h, int s, int Ls) { return h * Ls + slice_pos(s, Ls); }
+
 // ---------------------------------------------------------------------------
 // Storage policies.  load/store one 5D site (index n) of one half-field.
 // ---------------------------------------------------------------------------
 struct Store64 {
   using T = double;
   static constexpr int kPrec = P64;
+  static constexpr int kChunks = 12;     // 16-byte chunks per 5D site
+  static constexpr bool kScaled = false;
   __device__ static void load(const void* base, int n, int N5, Spinor<double>& o) {
     const double2* b = reinterpret_cast<const double2*>(base);
 #pragma unroll
@@ -78,6 +88,15 @@ struct Store64 {
       o.c[k + 6 * chir] = cmake(v.x, v.y);
     }
   }
+  // the 6 complex components of one chirality into o[0..5]
+  __device__ static void load_half(const void* base, int n, int N5, int chir, cplx<double>* o) {
+    const double2* b = reinterpret_cast<const double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      double2 v = __ldg(b + (size_t)(k + 6 * chir) * N5 + n);
+      o[k] = cmake(v.x, v.y);
+    }
+  }
   __device__ static void store(void* base, int n, int N5, const Spinor<double>& o) {
     double2* b = reinterpret_cast<double2*>(base);
 #pragma unroll
@@ -88,6 +107,8 @@ struct Store64 {
 struct Store32 {
   using T = float;
   static constexpr int kPrec = P32;
+  static constexpr int kChunks = 6;
+  static constexpr bool kScaled = false;
   __device__ static void load(const void* base, int n, int N5, Spinor<float>& o) {
     const float4* b = reinterpret_cast<const float4*>(base);
 #pragma unroll
@@ -106,6 +127,15 @@ struct Store32 {
       o.c[2 * k + 1 + 6 * chir] = cmake(v.z, v.w);
     }
   }
+  __device__ static void load_half(const void* base, int n, int N5, int chir, cplx<float>* o) {
+    const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      float4 v = __ldg(b + (size_t)(k + 3 * chir) * N5 + n);
+      o[2 * k] = cmake(v.x, v.y);
+      o[2 * k + 1] = cmake(v.z, v.w);
+    }
+  }
   __device__ static void store(void* base, int n, int N5, const Spinor<float>& o) {
     float4* b = reinterpret_cast<float4*>(base);
 #pragma unroll
@@ -121,6 +151,8 @@ template <bool BF>
 struct Store16 {
   using T = float;
   static constexpr int kPrec = BF ? PB16 : P16;
+  static constexpr int kChunks = 3;
+  static constexpr bool kScaled = true;
   __device__ static float to_f(uint16_t v) {
     if (BF) return __bfloat162float(__ushort_as_bfloat16(v));
     return __half2float(__ushort_as_half(v));
@@ -144,6 +176,23 @@ struct Store16 {
   }
   __device__ static void load_chir(const void* base, int n, int N5, int chir, Spinor<float>& o) {
     load(base, n, N5, o);
+  }
+  // chirality 0: complex 0..5 = chunk 0 (0..3) + low half of chunk 1 (4, 5);
+  // chirality 1: complex 6..11 = high half of chunk 1 (6, 7) + chunk 2 (8..11).
+  __device__ static void load_half(const void* base, int n, int N5, int chir, cplx<float>* o) {
+    const uint4* b = reinterpret_cast<const uint4*>(base);
+    const float sc = __ldg(reinterpret_cast<const float*>(b + (size_t)3 * N5) + n);
+    const uint4 v1 = __ldg(b + (size_t)N5 + n);
+    const uint4 v0 = __ldg(b + (size_t)(chir ? 2 : 0) * N5 + n);
+    uint32_t w[6];
+    if (chir == 0) {
+      w[0] = v0.x; w[1] = v0.y; w[2] = v0.z; w[3] = v0.w; w[4] = v1.x; w[5] = v1.y;
+    } else {
+      w[0] = v1.z; w[1] = v1.w; w[2] = v0.x; w[3] = v0.y; w[4] = v0.z; w[5] = v0.w;
+    }
+#pragma unroll
+    for (int q = 0; q < 6; q++)
+      o[q] = cmake(sc * to_f((uint16_t)(w[q] & 0xffffu)), sc * to_f((uint16_t)(w[q] >> 16)));
   }
   __device__ static void store(void* base, int n, int N5, const Spinor<float>& o) {
     uint4* b = reinterpret_cast<uint4*>(base);
@@ -170,6 +219,7 @@ struct Store16 {
 // ---------------------------------------------------------------------------
 struct Gauge64 {
   using T = double;
+  static constexpr int kLinkBytes = 144;
   __device__ static void load(const void* base, int h, int mu, Link<double>& U) {
     const double2* b = reinterpret_cast<const double2*>(base) + ((size_t)h * 4 + mu) * 9;
 #pragma unroll
@@ -181,6 +231,7 @@ struct Gauge64 {
 };
 struct Gauge32 {
   using T = float;
+  static constexpr int kLinkBytes = 80;
   __device__ static void load(const void* base, int h, int mu, Link<float>& U) {
     const float4* b = reinterpret_cast<const float4*>(base) + ((size_t)h * 4 + mu) * 5;
     float f[20];
@@ -198,6 +249,7 @@ struct Gauge32 {
 };
 struct Gauge16 {
   using T = float;
+  static constexpr int kLinkBytes = 48;
   __device__ static void load(const void* base, int h, int mu, Link<float>& U) {
     const uint4* b = reinterpret_cast<const uint4*>(base) + ((size_t)h * 4 + mu) * 3;
     uint32_t w[12];

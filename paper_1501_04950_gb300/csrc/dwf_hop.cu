@@ -84,11 +84,11 @@ __device__ __forceinline__ void hop_term(const Geom& g, const Coords& c, int h, 
   int sign;
   const int hn = neighbour(g, c, MU, DIR, sign);
   Spinor<T> in;
-  SP::load(v, hn * g.Ls + s, g.N5, in);
+  SP::load(v, site5(hn, s, g.Ls), g.N5, in);
   if (PRE == PRE_B) {
     Spinor<T> a, b;
-    SP::load_chir(v, hn * g.Ls + sp, g.N5, 0, a);
-    SP::load_chir(v, hn * g.Ls + sn, g.N5, 1, b);
+    SP::load_chir(v, site5(hn, sp, g.Ls), g.N5, 0, a);
+    SP::load_chir(v, site5(hn, sn, g.Ls), g.N5, 1, b);
 #pragma unroll
     for (int k = 0; k < 6; k++) {
       in.c[k] = cmake(fma(bd[0], in.c[k].re, bo[0] * a.c[k].re), fma(bd[0], in.c[k].im, bo[0] * a.c[k].im));
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const Geom g, const HopArgs<ty
   if (LOC == LOC_ID) {
     if (active) {
       Spinor<T> w;
-      SP::load(reinterpret_cast<const char*>(a.w) + off, h * Ls + s, g.N5, w);
+      SP::load(reinterpret_cast<const char*>(a.w) + off, site5(h, s, Ls), g.N5, w);
 #pragma unroll
       for (int k = 0; k < 12; k++)
         res.c[k] = cmake(fma(a.c_loc, w.c[k].re, res.c[k].re), fma(a.c_loc, w.c[k].im, res.c[k].im));
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const Geom g, const HopArgs<ty
     Spinor<T> w;
 #pragma unroll
     for (int k = 0; k < 12; k++) w.c[k] = cmake<T>(0, 0);
-    if (active) SP::load(reinterpret_cast<const char*>(a.w) + off, h * Ls + s, g.N5, w);
+    if (active) SP::load(reinterpret_cast<const char*>(a.w) + off, site5(h, s, Ls), g.N5, w);
     if (POST) __syncthreads();  // everyone is done reading sbuf
     put_site(sbuf + j * SST + s * 24, w);
     __syncthreads();
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const Geom g, const HopArgs<ty
     for (int k = 0; k < 12; k++)
       res.c[k] = cmake(fma(a.c_loc, lw.c[k].re, res.c[k].re), fma(a.c_loc, lw.c[k].im, res.c[k].im));
   }
-  if (active) SP::store(reinterpret_cast<char*>(a.out) + off, h * Ls + s, g.N5, res);
+  if (active) SP::store(reinterpret_cast<char*>(a.out) + off, site5(h, s, Ls), g.N5, res);
   if (NORM) {
     double v = active ? (double)sq(res) : 0.0;
     block_reduce_finish(v, a.red, rhs, gridDim.x, blockIdx.x);
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256) local_kernel(const Geom g, void* out, con
   Spinor<T> x;
 #pragma unroll
   for (int k = 0; k < 12; k++) x.c[k] = cmake<T>(0, 0);
-  if (active) SP::load(reinterpret_cast<const char*>(in) + off, h * Ls + s, g.N5, x);
+  if (active) SP::load(reinterpret_cast<const char*>(in) + off, site5(h, s, Ls), g.N5, x);
   if (g5in) {
 #pragma unroll
     for (int k = 6; k < 12; k++) x.c[k] = cmake(-x.c[k].re, -x.c[k].im);
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(256) local_kernel(const Geom g, void* out, con
   contract(smat, sbuf + j * SST, Ls, s, res);
 #pragma unroll
   for (int k = 0; k < 12; k++) res.c[k] = cmake(c * res.c[k].re, c * res.c[k].im);
-  if (active) SP::store(reinterpret_cast<char*>(out) + off, h * Ls + s, g.N5, res);
+  if (active) SP::store(reinterpret_cast<char*>(out) + off, site5(h, s, Ls), g.N5, res);
   if (do_norm) {
     double v = active ? (double)sq(res) : 0.0;
     block_reduce_finish(v, red, rhs, gridDim.x, blockIdx.x);
@@ -393,7 +393,19 @@ int hop_grid_blocks(const Geom& g, int prec, int block_sites) {
   return (g.Vh + S - 1) / S;
 }
 
+int g_disable_tuned = 0;
+
 cudaError_t launch_hop(const Geom& g, const HopLaunch& L, cudaStream_t st) {
+  if (!g_disable_tuned) {
+    cudaError_t e = cudaErrorNotSupported;
+    switch (L.prec) {
+      case P64: e = launch_hop2_f64(g, L, st); break;
+      case P32: e = launch_hop2_f32(g, L, st); break;
+      case P16: e = launch_hop2_f16(g, L, st); break;
+      case PB16: e = launch_hop2_bf16(g, L, st); break;
+    }
+    if (e != cudaErrorNotSupported) return e;
+  }
   switch (L.prec) {
     case P64: return dispatch_hop<Store64>(g, L, st);
     case P32: return dispatch_hop<Store32>(g, L, st);
@@ -404,6 +416,16 @@ cudaError_t launch_hop(const Geom& g, const HopLaunch& L, cudaStream_t st) {
 }
 
 cudaError_t launch_local(const Geom& g, const LocalLaunch& L, cudaStream_t st) {
+  if (!g_disable_tuned) {
+    cudaError_t e = cudaErrorNotSupported;
+    switch (L.prec) {
+      case P64: e = launch_hop2_f64_local(g, L, st); break;
+      case P32: e = launch_hop2_f32_local(g, L, st); break;
+      case P16: e = launch_hop2_f16_local(g, L, st); break;
+      case PB16: e = launch_hop2_bf16_local(g, L, st); break;
+    }
+    if (e != cudaErrorNotSupported) return e;
+  }
   switch (L.prec) {
     case P64: return run_local<Store64>(g, L, st);
     case P32: return run_local<Store32>(g, L, st);

@@ -1,9 +1,10 @@
 // dwf_internal.cuh -- layouts, geometry and kernel launchers shared by the
 // translation units of libdwf (GB300, sm_103a).
 //
-// Internal half-field layout (5th dimension innermost, s fastest):
-//   5D index n = h * Ls + s, h the half-lattice site index of the canonical
-//   layout; N5 = Vh * Ls.  Components are stored chunk-major so that a warp
+// Internal half-field layout (5th dimension innermost):
+//   5D index n = h * Ls + slice_pos(s), h the half-lattice site index of the
+//   canonical layout, slice_pos placing the even slices of a site before the
+//   odd ones (dwf_fields.cuh); N5 = Vh * Ls.  Components are stored chunk-major so that a warp
 //   reading one chunk of 32 consecutive n touches 512 contiguous bytes:
 //     FP64  double2 [12][N5]   (one complex per chunk, spin-major: spin*3+colour)
 //     FP32  float4  [6][N5]    (two complex per chunk)
@@ -78,8 +79,21 @@ struct HopLaunch {
   int g5out;
   const Reduce* red;        // nullptr: no norm
   int block_sites;          // 4D sites per CTA (0: default)
+  // Tuned path (Ls in {8, 12, 16}): 5th-dimension operators as chain programs
+  // (hop2::PR_*) over the recurrence coefficient block, and the neighbour table.
+  int post_prog;
+  int loc_prog;
+  const void* chain;        // hop2 chain coefficient block in the compute type
+  const int* nbr;           // [2 parities][Vh][8] neighbour half indices, bit 31 = sign
+  int* err;                 // device flag set when a bounded wait gives up
+  int use_tma;              // 1: stage neighbours through shared memory with bulk copies
 };
+// Tries the tuned kernel first, then the generic one.
 cudaError_t launch_hop(const Geom& g, const HopLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_f64(const Geom& g, const HopLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_f32(const Geom& g, const HopLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_f16(const Geom& g, const HopLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_bf16(const Geom& g, const HopLaunch& a, cudaStream_t s);
 int hop_grid_blocks(const Geom& g, int prec, int block_sites);
 
 // ---- site-local dense contraction: out = c * M (gamma5^g5in in) ---------------
@@ -93,8 +107,16 @@ struct LocalLaunch {
   double c;
   int g5in;
   const Reduce* red;
+  int prog;                 // hop2::PR_* equivalent of m (tuned path)
+  const void* chain;
 };
 cudaError_t launch_local(const Geom& g, const LocalLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_f64_local(const Geom& g, const LocalLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_f32_local(const Geom& g, const LocalLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_f16_local(const Geom& g, const LocalLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_bf16_local(const Geom& g, const LocalLaunch& a, cudaStream_t s);
+// Set to 1 to force the generic kernels (tests compare both paths).
+extern int g_disable_tuned;
 
 // ---- conversions ---------------------------------------------------------------
 size_t field_bytes(const Geom& g, int prec);

@@ -117,3 +117,44 @@ def test_dbb_adjoint_identity_fp64():
     lhs = np.vdot(u.ravel(), dv.ravel())
     rhs = np.vdot(du.ravel(), v.ravel())
     assert abs(lhs - rhs) < 1e-13 * abs(lhs)
+
+
+@pytest.mark.parametrize("Ls", [8, 12, 16])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_tuned_matches_generic(Ls, prec, monkeypatch):
+    """The tuned kernels (Ls in {8, 12, 16}) against the generic dense ones."""
+    sysm = make_case((4, 2, 4, 6), Ls, "varying", alpha=1.4, bc_t=-1)
+    psi = gaussian_half5d(sysm.lattice, Ls, seed=8)
+    outs = []
+    for generic in (False, True):
+        if generic:
+            monkeypatch.setenv("DWF_GENERIC_KERNELS", "1")
+        else:
+            monkeypatch.delenv("DWF_GENERIC_KERNELS", raising=False)
+        op = _op(sysm)
+        outs.append((_apply(op, psi, prec), _apply(op, psi, prec, dag=True)))
+        op.close()
+    monkeypatch.delenv("DWF_GENERIC_KERNELS", raising=False)
+    tol = {0: 1e-13, 1: 2e-6, 2: 1e-2}[prec]
+    for k in range(2):
+        assert site_norm_error(outs[0][k], outs[1][k]) <= tol
+
+
+@pytest.mark.parametrize("Ls", [8, 12, 16])
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_staged_matches_direct_loads(Ls, prec, monkeypatch):
+    """Bulk-copy staged neighbours (DWF_TMA=1) against direct loads: bitwise equal."""
+    sysm = make_case((4, 4, 2, 6), Ls, "varying", alpha=0.8, bc_t=-1, black=1)
+    psi = gaussian_half5d(sysm.lattice, Ls, seed=9)
+    outs = []
+    for staged in (False, True):
+        if staged:
+            monkeypatch.setenv("DWF_TMA", "1")
+        else:
+            monkeypatch.delenv("DWF_TMA", raising=False)
+        op = _op(sysm)
+        outs.append((_apply(op, psi, prec), _apply(op, psi, prec, dag=True)))
+        op.close()
+    monkeypatch.delenv("DWF_TMA", raising=False)
+    for k in range(2):
+        assert np.array_equal(outs[0][k], outs[1][k])
