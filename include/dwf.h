@@ -132,6 +132,22 @@ int dwf_unpack_half(dwf_handle h, double* dst_canonical, const void* src_interna
  * in and out must not overlap. */
 int dwf_apply_Dbb(dwf_handle h, void* out, const void* in, int prec, int nrhs, dwf_stream s);
 
+/* Same as dwf_apply_Dbb, for callers that cannot allocate device memory (a
+ * pool allocator owns the device, or cudaMalloc's implicit synchronisation is
+ * not acceptable in their loop).  The paper has no counterpart: this is a
+ * library service.  The red intermediate field lives in a static device array
+ * of DWF_NOALLOC_SCRATCH_BYTES compiled into the library (every GPU that loads
+ * the library holds it until exit) instead of handle workspace; no call
+ * allocates or frees anything.  Requires nrhs * dwf_field_bytes(prec) <=
+ * DWF_NOALLOC_SCRATCH_BYTES, else DWF_ERR_INVALID_ARG.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and caches
+ * it; make that first call before any stream capture.  All calls share the
+ * array and each call overwrites it completely, so calls that overlap on the
+ * GPU (other streams, other handles) race. */
+#define DWF_NOALLOC_SCRATCH_BYTES (32u << 20)
+int dwf_apply_Dbb_noalloc(dwf_handle h, void* out, const void* in, int prec, int nrhs,
+                          dwf_stream s);
+
 /* out = D_bb^dagger in = gamma5 [1 - 1/4 B^T H_br K^T H_rb I^-T] gamma5 in: the
  * adjoint of Eq. redblack (H is gamma5-hermitian; B, C, I are real and commute
  * with gamma5).  in and out must not overlap. */

@@ -1038,3 +1038,28 @@ int dwf_force(dwf_handle h, double* dSdU, const double* phi_half, const double* 
 }
 
 }  // extern "C"
+
+namespace dwf {
+
+int set_error(dwf_handle h, int code, const char* msg) { return fail(h, code, msg); }
+
+// D_bb apply with a caller-supplied red intermediate field of at least
+// nrhs * field_bytes(prec) bytes; allocates nothing (the handle's matrices for
+// its own alpha and m exist since dwf_create).
+int apply_dbb_with_scratch(dwf_handle h, void* out, const void* in, int prec, int nrhs,
+                           void* scratch, size_t scratch_bytes, cudaStream_t s) {
+  if (!h || !out || !in || !valid_prec(prec) || nrhs < 1 || out == in)
+    return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  if (!h->gauge_loaded) return fail(h, DWF_ERR_STATE, "gauge field not loaded");
+  const size_t need = field_bytes(h->g, prec) * (size_t)nrhs;
+  if (need > scratch_bytes)
+    return fail(h, DWF_ERR_INVALID_ARG,
+                "dwf_apply_Dbb_noalloc: the red intermediate field needs " + std::to_string(need) +
+                    " bytes, more than the " + std::to_string(scratch_bytes) +
+                    "-byte static scratch buffer; use dwf_apply_Dbb");
+  auto it = h->mats.find(std::make_pair(h->alpha, h->m));
+  if (it == h->mats.end()) return fail(h, DWF_ERR_STATE, "operator matrices missing");
+  return apply_dbb(h, it->second, prec, out, in, scratch, nrhs, nullptr, s);
+}
+
+}  // namespace dwf

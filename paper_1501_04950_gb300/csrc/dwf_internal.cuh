@@ -176,3 +176,10 @@ cudaError_t launch_force_project(const Geom& g, double* F, const double* U, cons
                                  int projected, cudaStream_t s);
 
 }  // namespace dwf
+
+typedef struct dwf_ctx* dwf_handle_internal;
+namespace dwf {
+int apply_dbb_with_scratch(dwf_handle_internal h, void* out, const void* in, int prec, int nrhs,
+                           void* scratch, size_t scratch_bytes, cudaStream_t s);
+int set_error(dwf_handle_internal h, int code, const char* msg);
+}  // namespace dwf

@@ -48,7 +48,9 @@ EXPORTS = [
     "dwf_default_options", "dwf_create", "dwf_destroy", "dwf_last_error", "dwf_field_bytes",
     "dwf_load_gauge", "dwf_pack_half", "dwf_unpack_half", "dwf_apply_Dbb", "dwf_apply_Dbb_dag",
     "dwf_apply_dalpha", "dwf_cgne_solve", "dwf_solve_normal", "dwf_force",
+    "dwf_apply_Dbb_noalloc",
 ]
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 def load_library(path: str = LIB_PATH):
@@ -68,6 +70,7 @@ def load_library(path: str = LIB_PATH):
         "dwf_unpack_half": (I, [P, P, P, I, I, P]),
         "dwf_apply_Dbb": (I, [P, P, P, I, I, P]),
         "dwf_apply_Dbb_dag": (I, [P, P, P, I, I, P]),
+        "dwf_apply_Dbb_noalloc": (I, [P, P, P, I, I, P]),
         "dwf_apply_dalpha": (I, [P, P, P, D, D, P]),
         "dwf_cgne_solve": (I, [P, P, P, P, I, ctypes.POINTER(D), ctypes.POINTER(Stats), P]),
         "dwf_solve_normal": (I, [P, P, P, ctypes.POINTER(Stats), P]),
@@ -168,6 +171,11 @@ class DWF:
     # --- operators ------------------------------------------------------------
     def apply_Dbb(self, out, inp, prec, nrhs=1):
         self._check(self.lib.dwf_apply_Dbb(self.h, _ptr(out), _ptr(inp), prec, nrhs, _stream()))
+
+    def apply_Dbb_noalloc(self, out, inp, prec, nrhs=1):
+        """D_bb through the entry point that allocates nothing (static scratch)."""
+        self._check(self.lib.dwf_apply_Dbb_noalloc(self.h, _ptr(out), _ptr(inp), prec, nrhs,
+                                                   _stream()))
 
     def apply_Dbb_dag(self, out, inp, prec, nrhs=1):
         self._check(self.lib.dwf_apply_Dbb_dag(self.h, _ptr(out), _ptr(inp), prec, nrhs, _stream()))
