@@ -672,6 +672,93 @@ int cgnr_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxiter, 
   return DWF_OK;
 }
 
+// CG on A x = phi with A = D_bb^+ D_bb (Hestenes-Stiefel), inner precision prec
+// with FP64 reliable updates of the normal residual phi - A x_hi.  phi in
+// W.b_hi, solution in W.x_hi (FP64 black fields).  Per iteration: w = D p
+// (|w|^2 = p^+ A p), z = D^+ w, x += a p, r -= a z, p = r + beta p.
+int cgnormal_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxiter, double delta,
+                   SolveWork& W, void* t64b, dwf_stats* st, cudaStream_t s) {
+  const int xprec = (prec == P16 || prec == PB16) ? P32 : prec;
+  const size_t f64 = field_bytes(h->g, P64), fi = field_bytes(h->g, prec),
+               fx = field_bytes(h->g, xprec);
+  Reduce red_ww = make_reduce(h, 0, S_WW);
+  Reduce red_rr[2] = {make_reduce(h, 1, S_ZZ0), make_reduce(h, 1, S_ZZ1)};
+  Reduce red_hi = make_reduce(h, 3, S_RRHI), red_bb = make_reduce(h, 3, S_BB);
+  int rc;
+  const long long launches0 = h->launches;
+  int n_app = 0, n_dag = 0, n_64 = 0;
+  CUCHK(h, cudaMemsetAsync(W.x_hi, 0, f64, s));
+  CUCHK(h, cudaMemsetAsync(W.xlo, 0, fx, s));
+  KLAUNCH(h, launch_convert(h->g, P64, W.r_hi, P64, W.b_hi, 1, f64, f64, &red_bb, s));
+  int cur = 0;
+  KLAUNCH(h, launch_convert(h->g, prec, W.r, P64, W.b_hi, 1, fi, f64, &red_rr[cur], s));
+  if ((rc = sync_read(h, 1, s))) return rc;
+  const double bb = h->pinned[S_BB];
+  auto fill = [&](int it, int restarts, double res) {
+    if (!st) return;
+    st->iterations = it;
+    st->restarts = restarts;
+    st->true_resid = res;
+    st->applies = n_app;
+    st->applies_dag = n_dag;
+    st->applies_fp64 = n_64;
+    st->kernel_launches = (int)(h->launches - launches0);
+  };
+  if (!(bb > 0.0)) {
+    fill(0, 0, 0.0);
+    return bb == 0.0 ? DWF_OK : fail(h, DWF_ERR_BREAKDOWN, "source norm is not finite");
+  }
+  const double bnorm = std::sqrt(bb);
+  CUCHK(h, cudaMemcpyAsync(W.p, W.r, fi, cudaMemcpyDeviceToDevice, s));
+  double rmax = bnorm, true_res = 1.0;
+  int it = 0, restarts = 0;
+  bool converged = false;
+  const int check = std::max(1, h->opt.check_every);
+  while (it < maxiter) {
+    if ((rc = apply_dbb(h, ms, prec, W.w, W.p, W.tr, 1, &red_ww, s))) return rc;
+    if ((rc = apply_dbb_dag(h, ms, prec, W.z, W.w, W.tr, W.tb, 1, nullptr, s))) return rc;
+    n_app++;
+    n_dag++;
+    const int nxt = 1 - cur;
+    KLAUNCH(h, launch_xr_update(h->g, prec, xprec, W.xlo, W.r, W.p, W.z,
+                                h->scal + (cur ? S_ZZ1 : S_ZZ0), h->scal + S_WW, kScal, 1, fx, fi,
+                                &red_rr[nxt], s));
+    it++;
+    if (it % check == 0 || it >= maxiter) {
+      if ((rc = sync_read(h, 1, s))) return rc;
+      const double rr = h->pinned[nxt ? S_ZZ1 : S_ZZ0], ww = h->pinned[S_WW];
+      if (!std::isfinite(rr) || !std::isfinite(ww) || !(ww > 0.0)) {
+        fill(it, restarts, true_res);
+        return fail(h, DWF_ERR_BREAKDOWN, "CG breakdown (p^+ A p <= 0 or not finite)");
+      }
+      const double rn = std::sqrt(rr);
+      if (rn < delta * rmax || rn <= tol * bnorm || it >= maxiter) {
+        KLAUNCH(h, launch_accumulate64(h->g, W.x_hi, xprec, W.xlo, 1, 1, f64, fx, s));
+        if ((rc = apply_dbb(h, ms, P64, W.t64, W.x_hi, W.t64r, 1, nullptr, s))) return rc;
+        if ((rc = apply_dbb_dag(h, ms, P64, t64b, W.t64, W.t64r, W.r_hi, 1, nullptr, s))) return rc;
+        n_64 += 2;
+        KLAUNCH(h, launch_sub64_norm(h->g, W.r_hi, W.b_hi, t64b, 1, f64, &red_hi, s));
+        KLAUNCH(h, launch_convert(h->g, prec, W.r, P64, W.r_hi, 1, fi, f64, &red_rr[nxt], s));
+        if ((rc = sync_read(h, 1, s))) return rc;
+        true_res = std::sqrt(h->pinned[S_RRHI]) / bnorm;
+        rmax = std::sqrt(h->pinned[S_RRHI]);
+        restarts++;
+        if (true_res <= tol) {
+          converged = true;
+          break;
+        }
+        if (it >= maxiter) break;
+      }
+    }
+    KLAUNCH(h, launch_p_update(h->g, prec, W.p, W.r, h->scal + (nxt ? S_ZZ1 : S_ZZ0),
+                               h->scal + (cur ? S_ZZ1 : S_ZZ0), kScal, 1, fi, s));
+    cur = nxt;
+  }
+  fill(it, restarts, true_res);
+  if (!converged) return fail(h, DWF_ERR_NOT_CONVERGED, "CG did not reach the tolerance within maxiter");
+  return DWF_OK;
+}
+
 int solver_params(dwf_ctx* h, int* prec, double* delta, bool* restart) {
   *prec = h->opt.precision_inner;
   *delta = h->opt.reliable_delta;
@@ -910,12 +997,31 @@ int dwf_apply_dalpha(dwf_handle h, double* out_full, const double* in_full, doub
 
 int dwf_solve_normal(dwf_handle h, double* x_half, const double* phi_half, dwf_stats* stats,
                      dwf_stream s) {
-  (void)h;
-  (void)x_half;
-  (void)phi_half;
-  (void)stats;
-  (void)s;
-  return fail(h, DWF_ERR_STATE, "not implemented");
+  if (!h || !x_half || !phi_half) return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  if (!h->gauge_loaded) return fail(h, DWF_ERR_STATE, "gauge field not loaded");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  int rc;
+  if ((rc = ensure_reduce(h, 1))) return rc;
+  int prec;
+  double delta;
+  bool restart;
+  solver_params(h, &prec, &delta, &restart);
+  SolveWork W;
+  if ((rc = alloc_solve_work(h, prec, W))) return rc;
+  void* t64b;
+  if ((rc = get_ws(h, "t64b", field_bytes(h->g, P64), &t64b))) return rc;
+  MatSet* ms;
+  if ((rc = build_matset(h, h->alpha, h->m, &ms))) return rc;
+  auto t0 = std::chrono::steady_clock::now();
+  KLAUNCH(h, launch_pack_half(h->g, P64, W.b_hi, phi_half, 1, st));
+  dwf_stats sk{};
+  rc = cgnormal_solve(h, *ms, prec, h->opt.rel_tol, h->opt.maxiter, delta, W, t64b, &sk, st);
+  if (rc && rc != DWF_ERR_NOT_CONVERGED) return rc;
+  KLAUNCH(h, launch_unpack_half(h->g, P64, x_half, W.x_hi, 1, st));
+  CUCHK(h, cudaStreamSynchronize(st));
+  sk.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = sk;
+  return rc;
 }
 
 int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* sol5d, int nrhs,
@@ -1029,12 +1135,79 @@ int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* so
 
 int dwf_force(dwf_handle h, double* dSdU, const double* phi_half, const double* X_half,
               int projected, dwf_stream s) {
-  (void)dSdU;
-  (void)phi_half;
-  (void)X_half;
-  (void)projected;
-  (void)s;
-  return fail(h, DWF_ERR_STATE, "not implemented");
+  if (!h || !dSdU || !phi_half) return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  if (!h->gauge_loaded) return fail(h, DWF_ERR_STATE, "gauge field not loaded");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  const Geom& g = h->g;
+  int rc;
+  MatSet* ms;
+  if ((rc = build_matset(h, h->alpha, h->m, &ms))) return rc;
+  const size_t f64 = field_bytes(g, P64);
+  const int black = h->opt.rb_parity, red = 1 - black;
+  void *X, *Y, *eta1, *xi1, *eta2;
+  if ((rc = get_ws(h, "f_Y", f64, &Y)) || (rc = get_ws(h, "f_eta1", f64, &eta1)) ||
+      (rc = get_ws(h, "f_xi1", f64, &xi1)) || (rc = get_ws(h, "f_eta2", f64, &eta2)) ||
+      (rc = get_ws(h, "f_red", f64, &X)))
+    return rc;
+  void* tred = X;  // red scratch of the FP64 applies
+  if (X_half) {
+    if ((rc = get_ws(h, "x_hi", f64, &X))) return rc;
+    KLAUNCH(h, launch_pack_half(g, P64, X, X_half, 1, st));
+  } else {
+    // recompute X = (D^+ D)^-1 phi (no solver history is kept)
+    if ((rc = ensure_reduce(h, 1))) return rc;
+    int prec;
+    double delta;
+    bool restart;
+    solver_params(h, &prec, &delta, &restart);
+    SolveWork W;
+    if ((rc = alloc_solve_work(h, prec, W))) return rc;
+    void* t64b;
+    if ((rc = get_ws(h, "t64b", f64, &t64b))) return rc;
+    KLAUNCH(h, launch_pack_half(g, P64, W.b_hi, phi_half, 1, st));
+    rc = cgnormal_solve(h, *ms, prec, h->opt.rel_tol, h->opt.maxiter, delta, W, t64b, nullptr, st);
+    if (rc) return rc;
+    X = W.x_hi;
+    tred = W.t64r;
+  }
+  // Y = D_bb X
+  if ((rc = apply_dbb(h, *ms, P64, Y, X, tred, 1, nullptr, st))) return rc;
+  // eta1 = I^-T Y
+  LocalLaunch Le{};
+  Le.prec = P64;
+  Le.out = eta1;
+  Le.in = Y;
+  Le.stride = f64;
+  Le.nrhs = 1;
+  Le.m = ms->ptr(P64, ms->mat_off(MatSet::IINVT));
+  Le.prog = hop2::PR_ITINV;
+  Le.chain = ms->ptr(P64, ms->chain_off());
+  Le.c = 1.0;
+  KLAUNCH(h, launch_local(g, Le, st));
+  // xi1 = I^-1 D_rb X = -1/2 I^-1 H_rb (B X)
+  HopLaunch Hx = base_hop(h, P64, red, 1, f64);
+  Hx.out = xi1;
+  Hx.v = X;
+  Hx.pre = PRE_B;
+  Hx.pre_diag = ms->ptr(P64, ms->bdiag_off());
+  Hx.pre_off = ms->ptr(P64, ms->boff_off());
+  Hx.post = ms->ptr(P64, ms->mat_off(MatSet::IINV));
+  Hx.c_hop = -0.5;
+  KLAUNCH(h, launch_hop(g, Hx, st));
+  // eta2 = I^-T D_br^+ eta1 = -1/2 K^T gamma5 H_rb (gamma5 eta1)
+  HopLaunch He = base_hop(h, P64, red, 1, f64);
+  He.out = eta2;
+  He.v = eta1;
+  He.pre = PRE_G5;
+  He.post = ms->ptr(P64, ms->mat_off(MatSet::KT));
+  He.g5out = 1;
+  He.c_hop = -0.5;
+  KLAUNCH(h, launch_hop(g, He, st));
+  KLAUNCH(h, launch_force(g, dSdU, eta1, xi1, eta2, X,
+                          reinterpret_cast<const double*>(ms->ptr(P64, ms->bdiag_off())),
+                          reinterpret_cast<const double*>(ms->ptr(P64, ms->boff_off())), h->gauge[0],
+                          gauge_bytes(g, P64) / 2, black, projected, st));
+  return DWF_OK;
 }
 
 }  // extern "C"

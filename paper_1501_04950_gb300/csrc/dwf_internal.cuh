@@ -168,12 +168,12 @@ cudaError_t launch_norm(const Geom& g, int prec, const void* x, int nrhs, size_t
 int blas_grid_blocks(const Geom& g);
 
 // ---- force (dwf_force.cu) -------------------------------------------------------
-// G_mu(x) += coef * sum_s [ eta(x)^+ (1-g_mu) . w(x+mu) + w(x)^+ ... ] outer products
-// (see the kernel for the exact form), eta on parity pe, w on parity 1-pe.
-cudaError_t launch_force_outer(const Geom& g, double* G, const void* eta, const void* w,
-                               int pe, double coef, cudaStream_t s);
-cudaError_t launch_force_project(const Geom& g, double* F, const double* U, const double* G,
-                                 int projected, cudaStream_t s);
+// dS/dU of S = phi^+ (D_bb^+ D_bb)^-1 phi from the auxiliary FP64 fields
+// eta1 = I^-T Y (black), xi1 = I^-1 D_rb X (red), eta2 = I^-T D_br^+ eta1 (red),
+// xi2 = X (black); out: canonical [V][4][3][3] complex128, raw G or TA(U G^+).
+cudaError_t launch_force(const Geom& g, double* out, const void* eta1, const void* xi1,
+                         const void* eta2, const void* xi2, const double* bd, const double* bo,
+                         const void* g64, size_t gpar, int black, int projected, cudaStream_t s);
 
 }  // namespace dwf
 
