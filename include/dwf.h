@@ -170,7 +170,9 @@ int dwf_apply_dalpha(dwf_handle h, double* out_full, const double* in_full, doub
  * The right-hand side is rhs = D_1(1) P b; red-black: r'_b = I^-1(rhs_b - D_br I^-1 rhs_r),
  * CG on D_bb^+ D_bb x = D_bb^+ r'_b to FP64 true residual opt.rel_tol, then
  * psi_r = I^-1 (rhs_r - D_rb psi_b).  Returns DWF_ERR_NOT_CONVERGED if any
- * source misses the tolerance within maxiter iterations. */
+ * source misses the tolerance within maxiter iterations, or if three
+ * consecutive FP64 residual replacements fail to lower the true residual by
+ * 10% (the tolerance is below what the arithmetic can reach). */
 int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* sol5d, int nrhs,
                    const double* alphas, dwf_stats* stats, dwf_stream s);
 

@@ -617,8 +617,8 @@ int cgnr_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxiter, 
   if ((rc = apply_inner_dag(W.z, W.r, &red_zz[cur]))) return rc;
   CUCHK(h, cudaMemcpyAsync(W.p, W.z, fi, cudaMemcpyDeviceToDevice, s));
   double rmax = bnorm;
-  int it = 0, restarts = 0;
-  double true_res = 1.0;
+  int it = 0, restarts = 0, stalled = 0;
+  double true_res = 1.0, best_res = 1.0;
   bool converged = false;
   const int check = std::max(1, h->opt.check_every);
   while (it < maxiter) {
@@ -651,6 +651,13 @@ int cgnr_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxiter, 
           converged = true;
           break;
         }
+        // stagnation: three residual replacements in a row without a 10% gain
+        if (true_res < 0.9 * best_res) {
+          best_res = true_res;
+          stalled = 0;
+        } else if (++stalled >= 3) {
+          break;
+        }
         if (it >= maxiter) break;
         if (restart) {
           cur = 0;
@@ -668,7 +675,9 @@ int cgnr_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxiter, 
   }
   if ((rc = timer_harvest(h))) return rc;
   fill_stats(it, restarts, true_res);
-  if (!converged) return fail(h, DWF_ERR_NOT_CONVERGED, "CG did not reach the tolerance within maxiter");
+  if (!converged)
+    return fail(h, DWF_ERR_NOT_CONVERGED,
+                "CG did not reach the tolerance (maxiter reached or the true residual stagnated)");
   return DWF_OK;
 }
 
@@ -710,8 +719,8 @@ int cgnormal_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxit
   }
   const double bnorm = std::sqrt(bb);
   CUCHK(h, cudaMemcpyAsync(W.p, W.r, fi, cudaMemcpyDeviceToDevice, s));
-  double rmax = bnorm, true_res = 1.0;
-  int it = 0, restarts = 0;
+  double rmax = bnorm, true_res = 1.0, best_res = 1.0;
+  int it = 0, restarts = 0, stalled = 0;
   bool converged = false;
   const int check = std::max(1, h->opt.check_every);
   while (it < maxiter) {
@@ -747,6 +756,12 @@ int cgnormal_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxit
           converged = true;
           break;
         }
+        if (true_res < 0.9 * best_res) {
+          best_res = true_res;
+          stalled = 0;
+        } else if (++stalled >= 3) {
+          break;
+        }
         if (it >= maxiter) break;
       }
     }
@@ -755,7 +770,9 @@ int cgnormal_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxit
     cur = nxt;
   }
   fill(it, restarts, true_res);
-  if (!converged) return fail(h, DWF_ERR_NOT_CONVERGED, "CG did not reach the tolerance within maxiter");
+  if (!converged)
+    return fail(h, DWF_ERR_NOT_CONVERGED,
+                "CG did not reach the tolerance (maxiter reached or the true residual stagnated)");
   return DWF_OK;
 }
 

@@ -8,7 +8,10 @@
   on 64 random links (one raw entry each, real and imaginary part) and along
   the 8 su(3) generators of 8 links;
 * through torch.autograd (FermionAction).
-FD tolerance: truncation O(h^2 S''') plus rounding ~1e-16 |S| / h; relative 1e-6.
+FD tolerance: the truncation error O(h^2 S''') is ~1e-10, but at this volume
+S = phi^+ X is ~1e5-1e6, so the FP64 rounding of S and the solver residual
+(X^+ r at rel_tol 1e-13) divided by 2h = 2e-5 leave an FD noise floor of
+~1e-5 on derivatives of order one: the bound is 1e-4 of max(1, |dS|).
 """
 import numpy as np
 import pytest
@@ -99,7 +102,7 @@ def test_config4_force_vs_finite_differences():
             want = G[t, z, y, x, mu, i, j].real if part == "re" else G[t, z, y, x, mu, i, j].imag
             rel = abs(fd - want) / max(1.0, abs(want))
             worst = max(worst, rel)
-            assert rel < 1e-6, (part, fd, want)
+            assert rel < 1e-4, (part, fd, want)
     # su(3) directions: dS/dh of S(exp(i h T_a) U) = i tr(T_a F)
     lam = np.zeros((8, 3, 3), dtype=np.complex128)
     lam[0][0, 1] = lam[0][1, 0] = 1
@@ -122,14 +125,16 @@ def test_config4_force_vs_finite_differences():
                 return uu
             fd = (_action(op_fd, rot(h), phit) - _action(op_fd, rot(-h), phit)) / (2 * h)
             want = (1j * np.trace(lam[a] / 2 @ F[t, z, y, x, mu])).real
-            assert abs(fd - want) / max(1.0, abs(want)) < 1e-6, (a, fd, want)
+            rel = abs(fd - want) / max(1.0, abs(want))
+            worst = max(worst, rel)
+            assert rel < 1e-4, (a, fd, want)
     print("config 4 FD worst relative error %.2e" % worst)
 
 
 def test_autograd_function():
     from paper_1501_04950_gb300.force import fermion_action
     sysm = make_case((4, 4, 2, 4), 8, "mobius", alpha=1.5, m=0.02)
-    op = _op(sysm)
+    op = _op(sysm, rel_tol=1e-12)
     U = torch.from_numpy(sysm.U).cuda().requires_grad_(True)
     phit = torch.from_numpy(gaussian_half5d(sysm.lattice, 8, seed=5)).cuda()
     S = fermion_action(U, phit, op)
