@@ -64,7 +64,7 @@ def peaks():
 
 def kernel_hash():
     h = hashlib.sha256()
-    for name in ["dwf_hop.cu", "dwf_fields.cuh", "dwf_internal.cuh"]:
+    for name in ["dwf_hop2.cuh", "dwf_fields.cuh", "dwf_internal.cuh"]:
         with open(os.path.join(ROOT, "paper_1501_04950_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

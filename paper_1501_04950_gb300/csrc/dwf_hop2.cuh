@@ -844,8 +844,12 @@ cudaError_t run(const Geom& g, const HopLaunch& L, cudaStream_t st) {
   const size_t smem = smem_bytes(LS, S, sizeof(T));
   constexpr int MB = min_blocks<T>();
   auto k = hop_kernel<SP, LS, PRE, POST, LOC, LOCP, G5, NORM, MB>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static bool attr = false;  // dynamic shared memory limit, set once per kernel
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   k<<<grid, block, smem, st>>>(g, a);
   return cudaGetLastError();
 }

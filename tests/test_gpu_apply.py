@@ -158,3 +158,33 @@ def test_staged_matches_direct_loads(Ls, prec, monkeypatch):
     monkeypatch.delenv("DWF_TMA", raising=False)
     for k in range(2):
         assert np.array_equal(outs[0][k], outs[1][k])
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 5e-6), (0, 1e-12)])
+def test_full_size_sampled_parity(prec, tol):
+    """16^3x32, Ls = 16 (the benchmark workload and its launch configuration):
+    the GPU D_bb at 24 sampled black sites against the single-site oracle."""
+    import oracle as O
+    from oracle.pointwise import PointwiseDbb
+    from synthetic import gauge_field
+    L, Ls = (16, 16, 16, 32), 16
+    sysm = O.DWFSystem(L, Ls, -1.8, 0.01, 1.0, np.full(Ls, 1.5), np.full(Ls, 0.5),
+                       gauge_field(L, 0.5, seed=0))
+    op = _op(sysm)
+    psi = gaussian_half5d(L, Ls, seed=2)
+    got = _apply(op, psi, prec)
+    pw = PointwiseDbb(sysm)
+    rng = np.random.default_rng(7)
+    refs, gots = [], []
+    while len(refs) < 24:
+        c = tuple(int(rng.integers(0, n)) for n in L)
+        if sum(c) % 2 != 0:
+            continue
+        lex = c[0] + 16 * (c[1] + 16 * (c[2] + 16 * c[3]))
+        refs.append(pw.dbb_at(psi, c))
+        gots.append(got[:, lex // 2])
+    refs = np.stack(refs, axis=1)
+    gots = np.stack(gots, axis=1)
+    rms = np.sqrt((np.abs(refs) ** 2).sum(axis=(-1, -2)).mean())
+    d = np.sqrt((np.abs(gots - refs) ** 2).sum(axis=(-1, -2)))
+    assert d.max() / rms <= tol, d.max() / rms
