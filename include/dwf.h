@@ -82,6 +82,8 @@ typedef struct {
   int solver;            /* DWF_SOLVER_* (default DWF_SOLVER_RELIABLE)               */
   int check_every;       /* iterations between convergence polls (default 16)        */
   int profile;           /* 1: time the inner applies with CUDA events (stats.apply_ms) */
+  int graph;             /* 1 (default): replay the CG iterations between polls as a CUDA graph */
+  int rhs_block;         /* right-hand sides solved together: 0 (default) = autotuned        */
 } dwf_options;
 
 typedef struct {
@@ -89,13 +91,14 @@ typedef struct {
   int restarts;          /* reliable updates / defect-correction cycles               */
   double true_resid;     /* FP64 |r'_b - D_bb x| / |r'_b| of the returned solution     */
   double true_resid_5d;  /* FP64 |rhs - D_alpha psi| / |rhs| of the full 5D solution    */
-  double seconds;        /* wall time of the solve                                     */
+  double seconds;        /* wall time from the start of the batch's CG to this source's
+                            convergence (its latency inside the batch)                  */
   int applies;           /* inner-precision D_bb applies                               */
   int applies_dag;       /* inner-precision D_bb^+ applies                             */
   int applies_fp64;      /* FP64 D_bb applies (true residuals)                          */
   int kernel_launches;   /* CUDA kernels the solve launched                             */
-  double apply_ms;       /* device time of the inner D_bb applies (opt.profile = 1)     */
-  double apply_dag_ms;   /* device time of the inner D_bb^+ applies (opt.profile = 1)   */
+  double apply_ms;       /* device time of the batch's inner D_bb applies (opt.profile = 1) */
+  double apply_dag_ms;   /* same for the D_bb^+ applies                                  */
 } dwf_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -158,6 +161,17 @@ int dwf_apply_Dbb_dag(dwf_handle h, void* out, const void* in, int prec, int nrh
  * operator of Sec. 2, Eq. mobius1, used for right-hand sides and checks. */
 int dwf_apply_dalpha(dwf_handle h, double* out_full, const double* in_full, double alpha,
                      double m, dwf_stream s);
+
+/* Batched solves: the nrhs sources are solved in blocks of rhs_block right-hand
+ * sides that share every kernel launch (each with its own alpha, scalars and
+ * convergence; converged ones are masked off).  With rhs_block = 0 a built-in
+ * autotuner times the batched D_bb apply for block sizes that fit in free
+ * device memory, and for the two neighbour staging variants, and keeps the
+ * fastest per right-hand side (cached per lattice, Ls, precision and nrhs in
+ * the process, and in the file named by DWF_AUTOTUNE_CACHE if set).  The CG
+ * iterations between two convergence polls (check_every, rounded up to even)
+ * are captured once as a CUDA graph and replayed.  All solver work runs on a
+ * stream owned by the handle; the call first waits for the caller's stream. */
 
 /* Solve D_alpha(m) P z = D_1(1) P b for nrhs sources b = (b_1, 0, ..., 0)
  * (Sec. 2 Eq. tosolve1, App. B Eq. tosolve) and return the 4D propagators

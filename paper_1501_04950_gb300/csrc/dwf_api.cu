@@ -17,6 +17,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <limits>
+#include <sstream>
 #include <map>
 #include <string>
 #include <vector>
@@ -218,6 +221,11 @@ struct dwf_ctx {
   std::vector<int> pending_kind;
   size_t next_event = 0;
   double timed_ms[2] = {0, 0};
+  cudaStream_t cstream = nullptr;  // solver stream (graph capture needs a non-legacy stream)
+  int* d_active = nullptr;         // per right-hand-side active mask of a batched solve
+  int* pinned_i = nullptr;         // host staging of the mask
+  int active_cap = 0;
+  std::map<std::string, std::pair<int, int>> tune;  // autotuned (rhs block, staging)
 };
 
 namespace {
@@ -385,39 +393,63 @@ HopLaunch base_hop(dwf_ctx* h, int prec, int p, int nrhs, size_t stride) {
   return L;
 }
 
+// Coefficient arrays of one or more right-hand sides: the layout (offsets) of a
+// MatSet, base pointers of the FP64 / FP32 copies, the element stride between
+// right-hand sides (0: all share one set) and the per-RHS active mask.
+struct CoefView {
+  const MatSet* layout;
+  const void* dev[2];
+  size_t cstride;
+  const int* active;
+  const void* ptr(int prec, size_t off) const {
+    const int f = prec == P64 ? 0 : 1;
+    return reinterpret_cast<const char*>(dev[f]) + off * (f == 0 ? 8 : 4);
+  }
+};
+CoefView view_of(const MatSet& ms) { return CoefView{&ms, {ms.dev[0], ms.dev[1]}, 0, nullptr}; }
+
+void set_coef(HopLaunch& L, const CoefView& cv) {
+  L.cstride = cv.cstride;
+  L.active = cv.active;
+}
+
 // out = D_bb in.  tmp: red half-field(s) of the same precision.
-int apply_dbb(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void* in, void* tmp, int nrhs,
+int apply_dbb(dwf_ctx* h, const CoefView& cv, int prec, void* out, const void* in, void* tmp, int nrhs,
               const Reduce* norm, cudaStream_t s) {
+  const MatSet& ms = *cv.layout;
   const int black = h->opt.rb_parity, red = 1 - black;
   const size_t st = field_bytes(h->g, prec);
   HopLaunch A = base_hop(h, prec, red, nrhs, st);
   A.out = tmp;
   A.v = in;
   A.pre = PRE_B;
-  A.pre_diag = ms.ptr(prec, ms.bdiag_off());
-  A.pre_off = ms.ptr(prec, ms.boff_off());
-  A.post = ms.ptr(prec, ms.mat_off(MatSet::K));
+  A.pre_diag = cv.ptr(prec, ms.bdiag_off());
+  A.pre_off = cv.ptr(prec, ms.boff_off());
+  A.post = cv.ptr(prec, ms.mat_off(MatSet::K));
   A.post_prog = hop2::PR_K;
-  A.chain = ms.ptr(prec, ms.chain_off());
+  A.chain = cv.ptr(prec, ms.chain_off());
+  set_coef(A, cv);
   KLAUNCH(h, launch_hop(h->g, A, s));
   HopLaunch B = base_hop(h, prec, black, nrhs, st);
   B.out = out;
   B.v = tmp;
   B.w = in;
-  B.post = ms.ptr(prec, ms.mat_off(MatSet::IINV));
+  B.post = cv.ptr(prec, ms.mat_off(MatSet::IINV));
   B.post_prog = hop2::PR_IINV;
-  B.chain = ms.ptr(prec, ms.chain_off());
+  B.chain = cv.ptr(prec, ms.chain_off());
   B.loc = LOC_ID;
   B.c_hop = -0.25;
   B.c_loc = 1.0;
   B.red = norm;
+  set_coef(B, cv);
   KLAUNCH(h, launch_hop(h->g, B, s));
   return DWF_OK;
 }
 
 // out = D_bb^+ in.  tmp_red: red field(s); tmp_blk: black field(s).
-int apply_dbb_dag(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void* in, void* tmp_red,
+int apply_dbb_dag(dwf_ctx* h, const CoefView& cv, int prec, void* out, const void* in, void* tmp_red,
                   void* tmp_blk, int nrhs, const Reduce* norm, cudaStream_t s) {
+  const MatSet& ms = *cv.layout;
   const int black = h->opt.rb_parity, red = 1 - black;
   const size_t st = field_bytes(h->g, prec);
   LocalLaunch L{};
@@ -426,31 +458,35 @@ int apply_dbb_dag(dwf_ctx* h, const MatSet& ms, int prec, void* out, const void*
   L.in = in;
   L.stride = st;
   L.nrhs = nrhs;
-  L.m = ms.ptr(prec, ms.mat_off(MatSet::IINVT));
+  L.m = cv.ptr(prec, ms.mat_off(MatSet::IINVT));
   L.prog = hop2::PR_ITINV;
-  L.chain = ms.ptr(prec, ms.chain_off());
+  L.chain = cv.ptr(prec, ms.chain_off());
   L.c = 1.0;
   L.g5in = 1;
+  L.cstride = cv.cstride;
+  L.active = cv.active;
   KLAUNCH(h, launch_local(h->g, L, s));
   HopLaunch A = base_hop(h, prec, red, nrhs, st);
   A.out = tmp_red;
   A.v = tmp_blk;
-  A.post = ms.ptr(prec, ms.mat_off(MatSet::KT));
+  A.post = cv.ptr(prec, ms.mat_off(MatSet::KT));
   A.post_prog = hop2::PR_KT;
-  A.chain = ms.ptr(prec, ms.chain_off());
+  A.chain = cv.ptr(prec, ms.chain_off());
+  set_coef(A, cv);
   KLAUNCH(h, launch_hop(h->g, A, s));
   HopLaunch B = base_hop(h, prec, black, nrhs, st);
   B.out = out;
   B.v = tmp_red;
   B.w = in;
-  B.post = ms.ptr(prec, ms.mat_off(MatSet::BT));
+  B.post = cv.ptr(prec, ms.mat_off(MatSet::BT));
   B.post_prog = hop2::PR_BT;
-  B.chain = ms.ptr(prec, ms.chain_off());
+  B.chain = cv.ptr(prec, ms.chain_off());
   B.loc = LOC_ID;
   B.c_hop = -0.25;
   B.c_loc = 1.0;
   B.g5out = 1;
   B.red = norm;
+  set_coef(B, cv);
   KLAUNCH(h, launch_hop(h->g, B, s));
   return DWF_OK;
 }
@@ -503,8 +539,8 @@ struct SolveWork {
   void *p, *r, *w, *z, *xlo, *tb, *tr;    // inner precision
 };
 
-int alloc_solve_work(dwf_ctx* h, int prec, SolveWork& W) {
-  const size_t f64 = field_bytes(h->g, P64), fi = field_bytes(h->g, prec);
+int alloc_solve_work(dwf_ctx* h, int prec, SolveWork& W, int nb = 1) {
+  const size_t f64 = field_bytes(h->g, P64) * nb, fi = field_bytes(h->g, prec) * nb;
   const std::string sfx = "_" + std::to_string(prec);
   int rc;
   if ((rc = get_ws(h, "b_hi", f64, &W.b_hi))) return rc;
@@ -517,10 +553,16 @@ int alloc_solve_work(dwf_ctx* h, int prec, SolveWork& W) {
   if ((rc = get_ws(h, "w" + sfx, fi, &W.w))) return rc;
   if ((rc = get_ws(h, "z" + sfx, fi, &W.z))) return rc;
   const int xprec = (prec == P16 || prec == PB16) ? P32 : prec;
-  if ((rc = get_ws(h, "xlo" + sfx, field_bytes(h->g, xprec), &W.xlo))) return rc;
+  if ((rc = get_ws(h, "xlo" + sfx, field_bytes(h->g, xprec) * nb, &W.xlo))) return rc;
   if ((rc = get_ws(h, "tb" + sfx, fi, &W.tb))) return rc;
   if ((rc = get_ws(h, "tr" + sfx, fi, &W.tr))) return rc;
   return DWF_OK;
+}
+
+// Bytes of solver workspace per right-hand side (used by the autotuner's memory check).
+size_t solve_bytes_per_rhs(const Geom& g, int prec) {
+  const int xprec = (prec == P16 || prec == PB16) ? P32 : prec;
+  return 5 * field_bytes(g, P64) + 6 * field_bytes(g, prec) + field_bytes(g, xprec);
 }
 
 // Start/stop events around one apply (kind 0: D_bb, 1: D_bb^+) when profiling.
@@ -532,7 +574,12 @@ int timer_mark(dwf_ctx* h, cudaStream_t s, bool start, int kind) {
     h->events.push_back(e);
   }
   const int idx = (int)h->next_event++;
-  CUCHK(h, cudaEventRecord(h->events[idx], s));
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CUCHK(h, cudaStreamIsCapturing(s, &cs));
+  if (cs == cudaStreamCaptureStatusActive)
+    CUCHK(h, cudaEventRecordWithFlags(h->events[idx], s, cudaEventRecordExternal));
+  else
+    CUCHK(h, cudaEventRecord(h->events[idx], s));
   if (start) {
     h->pending.push_back(idx);
     h->pending_kind.push_back(kind);
@@ -541,7 +588,8 @@ int timer_mark(dwf_ctx* h, cudaStream_t s, bool start, int kind) {
 }
 
 // After a stream synchronisation: add the elapsed time of all recorded pairs.
-int timer_harvest(dwf_ctx* h) {
+// keep = true for pairs recorded inside a CUDA graph (re-recorded at every replay).
+int timer_harvest(dwf_ctx* h, bool keep = false) {
   if (!h->opt.profile) return DWF_OK;
   for (size_t k = 0; k < h->pending.size(); k++) {
     float ms = 0.f;
@@ -549,20 +597,40 @@ int timer_harvest(dwf_ctx* h) {
     CUCHK(h, cudaEventElapsedTime(&ms, h->events[i], h->events[i + 1]));
     h->timed_ms[h->pending_kind[k]] += ms;
   }
-  h->pending.clear();
-  h->pending_kind.clear();
-  h->next_event = 0;
+  if (!keep) {
+    h->pending.clear();
+    h->pending_kind.clear();
+    h->next_event = 0;
+  }
   return DWF_OK;
 }
 
-// CG on D^+ D x = D^+ b (CGNR form: r = b - D x is tracked, z = D^+ r), inner
-// precision prec with FP64 reliable updates (residual replacement when |r|
-// drops below delta times its maximum since the last update) or, with
-// restart = true, FP64 defect correction (the inner CG restarts from p = z
-// after every update).  b_hi, x_hi: FP64 black fields; x_hi returned.  The
-// inner solution increment x_lo is kept in FP32 when prec is 16-bit.
-int cgnr_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxiter, double delta,
-               bool restart, SolveWork& W, dwf_stats* st, cudaStream_t s) {
+int ensure_active(dwf_ctx* h, int nb) {
+  if (h->active_cap >= nb) return DWF_OK;
+  if (h->d_active) {
+    cudaFree(h->d_active);
+    cudaFreeHost(h->pinned_i);
+  }
+  CUCHK(h, cudaMalloc(&h->d_active, sizeof(int) * nb));
+  CUCHK(h, cudaMallocHost(&h->pinned_i, sizeof(double) * (nb + 2)));
+  h->active_cap = nb;
+  return DWF_OK;
+}
+
+// CG on D^+ D x = D^+ b for nb right-hand sides at once (CGNR form: r = b - D x
+// is tracked, z = D^+ r), inner precision prec with FP64 reliable updates
+// (residual replacement once |r| drops below delta times its maximum since the
+// last replacement) or, with restart = true, FP64 defect correction (beta = 0
+// after every replacement).  One iteration:
+//   z = D^+ r (fused |z|^2), beta = |z|^2 / |z_prev|^2, p = z + beta p,
+//   w = D p (fused |w|^2), a = |z|^2 / |w|^2, x += a p, r -= a w (fused |r|^2);
+// the first beta is 0 (|z_prev|^2 starts at +inf).  The check iterations
+// between two convergence polls are captured once as a CUDA graph.  Each right-
+// hand side has its own scalars, coefficients (cv.cstride) and convergence; the
+// device mask skips converged ones.  W.b_hi holds the nb FP64 sources, W.x_hi
+// receives the solutions.
+int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int maxiter,
+                 double delta, bool restart, SolveWork& W, int nb, dwf_stats* st, cudaStream_t s) {
   const int xprec = (prec == P16 || prec == PB16) ? P32 : prec;
   const size_t f64 = field_bytes(h->g, P64), fi = field_bytes(h->g, prec),
                fx = field_bytes(h->g, xprec);
@@ -570,113 +638,218 @@ int cgnr_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxiter, 
   Reduce red_zz[2] = {make_reduce(h, 2, S_ZZ0), make_reduce(h, 2, S_ZZ1)};
   Reduce red_hi = make_reduce(h, 3, S_RRHI), red_bb = make_reduce(h, 3, S_BB);
   int rc;
+  if ((rc = ensure_active(h, nb))) return rc;
   const long long launches0 = h->launches;
   h->timed_ms[0] = h->timed_ms[1] = 0.0;
   h->pending.clear();
   h->pending_kind.clear();
   h->next_event = 0;
-  int n_app = 0, n_dag = 0, n_64 = 0;
-  auto apply_inner = [&](void* out, const void* in, const Reduce* red) -> int {
-    int r;
-    if ((r = timer_mark(h, s, true, 0))) return r;
-    if ((r = apply_dbb(h, ms, prec, out, in, W.tr, 1, red, s))) return r;
-    n_app++;
-    return timer_mark(h, s, false, 0);
+  std::vector<int> act(nb, 1), conv(nb, 0), its(nb, 0), rst(nb, 0), stalled(nb, 0), code(nb, 0);
+  std::vector<double> bnorm(nb), rmax(nb), true_res(nb, 1.0), best(nb, 1.0), t_done(nb, -1.0);
+  const auto t_start = std::chrono::steady_clock::now();
+  auto now_s = [&]() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   };
-  auto apply_inner_dag = [&](void* out, const void* in, const Reduce* red) -> int {
-    int r;
-    if ((r = timer_mark(h, s, true, 1))) return r;
-    if ((r = apply_dbb_dag(h, ms, prec, out, in, W.tr, W.tb, 1, red, s))) return r;
-    n_dag++;
-    return timer_mark(h, s, false, 1);
+  CoefView cv = cv_in;
+  cv.active = h->d_active;
+  auto push_active = [&]() -> int {
+    for (int r = 0; r < nb; r++) h->pinned_i[r] = act[r];
+    CUCHK(h, cudaMemcpyAsync(h->d_active, h->pinned_i, sizeof(int) * nb, cudaMemcpyHostToDevice, s));
+    return DWF_OK;
   };
-  auto fill_stats = [&](int it, int restarts, double true_res) {
-    if (!st) return;
-    st->iterations = it;
-    st->restarts = restarts;
-    st->true_resid = true_res;
-    st->applies = n_app;
-    st->applies_dag = n_dag;
-    st->applies_fp64 = n_64;
-    st->apply_ms = h->timed_ms[0];
-    st->apply_dag_ms = h->timed_ms[1];
-    st->kernel_launches = (int)(h->launches - launches0);
+  // |z_prev|^2 = +inf for the listed right-hand sides (first beta = 0)
+  double* inf_src = reinterpret_cast<double*>(h->pinned_i + ((nb + 1) & ~1));
+  auto reset_beta = [&](const std::vector<int>& which) -> int {
+    *inf_src = std::numeric_limits<double>::infinity();
+    for (int r = 0; r < nb; r++)
+      if (which[r])
+        CUCHK(h, cudaMemcpyAsync(h->scal + (size_t)r * kScal + S_ZZ0, inf_src, sizeof(double),
+                                 cudaMemcpyHostToDevice, s));
+    return DWF_OK;
   };
-  CUCHK(h, cudaMemsetAsync(W.x_hi, 0, f64, s));
-  CUCHK(h, cudaMemsetAsync(W.xlo, 0, fx, s));
-  KLAUNCH(h, launch_convert(h->g, P64, W.r_hi, P64, W.b_hi, 1, f64, f64, &red_bb, s));
-  KLAUNCH(h, launch_convert(h->g, prec, W.r, P64, W.b_hi, 1, fi, f64, nullptr, s));
-  if ((rc = sync_read(h, 1, s))) return rc;
-  const double bb = h->pinned[S_BB];
-  if (!(bb > 0.0)) {
-    fill_stats(0, 0, 0.0);
-    return bb == 0.0 ? DWF_OK : fail(h, DWF_ERR_BREAKDOWN, "source norm is not finite");
-  }
-  const double bnorm = std::sqrt(bb);
-  int cur = 0;
-  if ((rc = apply_inner_dag(W.z, W.r, &red_zz[cur]))) return rc;
-  CUCHK(h, cudaMemcpyAsync(W.p, W.z, fi, cudaMemcpyDeviceToDevice, s));
-  double rmax = bnorm;
-  int it = 0, restarts = 0, stalled = 0;
-  double true_res = 1.0, best_res = 1.0;
-  bool converged = false;
-  const int check = std::max(1, h->opt.check_every);
-  while (it < maxiter) {
-    if ((rc = apply_inner(W.w, W.p, &red_ww))) return rc;
-    KLAUNCH(h, launch_xr_update(h->g, prec, xprec, W.xlo, W.r, W.p, W.w,
-                                h->scal + (cur ? S_ZZ1 : S_ZZ0), h->scal + S_WW, kScal, 1, fx, fi,
-                                &red_rr, s));
-    it++;
-    if (it % check == 0 || it >= maxiter) {
-      if ((rc = sync_read(h, 1, s))) return rc;
-      if ((rc = timer_harvest(h))) return rc;
-      const double rr = h->pinned[S_RR], ww = h->pinned[S_WW];
-      if (!std::isfinite(rr) || !std::isfinite(ww) || !(ww > 0.0)) {
-        fill_stats(it, restarts, true_res);
-        return fail(h, DWF_ERR_BREAKDOWN, "CG breakdown (|Dp|^2 <= 0 or not finite)");
-      }
-      const double rn = std::sqrt(rr);
-      if (rn < delta * rmax || rn <= tol * bnorm || it >= maxiter) {
-        // reliable update: x_hi += x_lo, r = b - D x_hi in FP64
-        KLAUNCH(h, launch_accumulate64(h->g, W.x_hi, xprec, W.xlo, 1, 1, f64, fx, s));
-        if ((rc = apply_dbb(h, ms, P64, W.t64, W.x_hi, W.t64r, 1, nullptr, s))) return rc;
-        n_64++;
-        KLAUNCH(h, launch_sub64_norm(h->g, W.r_hi, W.b_hi, W.t64, 1, f64, &red_hi, s));
-        KLAUNCH(h, launch_convert(h->g, prec, W.r, P64, W.r_hi, 1, fi, f64, nullptr, s));
-        if ((rc = sync_read(h, 1, s))) return rc;
-        true_res = std::sqrt(h->pinned[S_RRHI]) / bnorm;
-        rmax = std::sqrt(h->pinned[S_RRHI]);
-        restarts++;
-        if (true_res <= tol) {
-          converged = true;
-          break;
-        }
-        // stagnation: three residual replacements in a row without a 10% gain
-        if (true_res < 0.9 * best_res) {
-          best_res = true_res;
-          stalled = 0;
-        } else if (++stalled >= 3) {
-          break;
-        }
-        if (it >= maxiter) break;
-        if (restart) {
-          cur = 0;
-          if ((rc = apply_inner_dag(W.z, W.r, &red_zz[cur]))) return rc;
-          CUCHK(h, cudaMemcpyAsync(W.p, W.z, fi, cudaMemcpyDeviceToDevice, s));
-          continue;
-        }
+  if ((rc = push_active())) return rc;
+  CUCHK(h, cudaMemsetAsync(W.x_hi, 0, f64 * nb, s));
+  CUCHK(h, cudaMemsetAsync(W.xlo, 0, fx * nb, s));
+  CUCHK(h, cudaMemsetAsync(W.p, 0, fi * nb, s));
+  KLAUNCH(h, launch_convert(h->g, P64, W.r_hi, P64, W.b_hi, nb, f64, f64, &red_bb, s));
+  KLAUNCH(h, launch_convert(h->g, prec, W.r, P64, W.b_hi, nb, fi, f64, nullptr, s));
+  if ((rc = reset_beta(act))) return rc;
+  if ((rc = sync_read(h, nb, s))) return rc;
+  for (int r = 0; r < nb; r++) {
+    const double bb = h->pinned[(size_t)r * kScal + S_BB];
+    bnorm[r] = std::sqrt(bb);
+    rmax[r] = bnorm[r];
+    if (!(bb > 0.0)) {
+      act[r] = 0;
+      if (bb == 0.0) {
+        conv[r] = 1;
+        true_res[r] = 0.0;
+      } else {
+        code[r] = DWF_ERR_BREAKDOWN;
       }
     }
-    const int nxt = 1 - cur;
-    if ((rc = apply_inner_dag(W.z, W.r, &red_zz[nxt]))) return rc;
-    KLAUNCH(h, launch_p_update(h->g, prec, W.p, W.z, h->scal + (nxt ? S_ZZ1 : S_ZZ0),
-                               h->scal + (cur ? S_ZZ1 : S_ZZ0), kScal, 1, fi, s));
-    cur = nxt;
   }
-  if ((rc = timer_harvest(h))) return rc;
-  fill_stats(it, restarts, true_res);
-  if (!converged)
-    return fail(h, DWF_ERR_NOT_CONVERGED,
+  if ((rc = push_active())) return rc;
+
+  auto enqueue_iter = [&](int cur) -> int {
+    const int nxt = 1 - cur;
+    int r;
+    if ((r = timer_mark(h, s, true, 1))) return r;
+    if ((r = apply_dbb_dag(h, cv, prec, W.z, W.r, W.tr, W.tb, nb, &red_zz[nxt], s))) return r;
+    if ((r = timer_mark(h, s, false, 1))) return r;
+    KLAUNCH(h, launch_p_update(h->g, prec, W.p, W.z, h->scal + (nxt ? S_ZZ1 : S_ZZ0),
+                               h->scal + (cur ? S_ZZ1 : S_ZZ0), kScal, nb, fi, s, h->d_active));
+    if ((r = timer_mark(h, s, true, 0))) return r;
+    if ((r = apply_dbb(h, cv, prec, W.w, W.p, W.tr, nb, &red_ww, s))) return r;
+    if ((r = timer_mark(h, s, false, 0))) return r;
+    KLAUNCH(h, launch_xr_update(h->g, prec, xprec, W.xlo, W.r, W.p, W.w,
+                                h->scal + (nxt ? S_ZZ1 : S_ZZ0), h->scal + S_WW, kScal, nb, fx, fi,
+                                &red_rr, s, h->d_active));
+    return DWF_OK;
+  };
+  int check = std::max(2, h->opt.check_every);
+  if (check & 1) check++;
+  const bool use_graph = h->opt.graph != 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long lpc = 0;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+  };
+  if (use_graph) {
+    const long long l0 = h->launches;
+    CUCHK(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    int cur = 0;
+    for (int k = 0; k < check; k++) {
+      if ((rc = enqueue_iter(cur))) {
+        cudaStreamEndCapture(s, &graph);
+        cleanup();
+        return rc;
+      }
+      cur = 1 - cur;
+    }
+    CUCHK(h, cudaStreamEndCapture(s, &graph));
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      cleanup();
+      return fail(h, DWF_ERR_CUDA, "cudaGraphInstantiate failed");
+    }
+    lpc = h->launches - l0;
+    h->launches = l0;
+  }
+  int it = 0;
+  bool any_active = std::any_of(act.begin(), act.end(), [](int a) { return a != 0; });
+  while (any_active && it < maxiter) {
+    if (use_graph) {
+      if (cudaGraphLaunch(exec, s) != cudaSuccess) {
+        cleanup();
+        return fail(h, DWF_ERR_CUDA, "cudaGraphLaunch failed");
+      }
+      h->launches += lpc;
+    } else {
+      int cur = 0;
+      for (int k = 0; k < check; k++) {
+        if ((rc = enqueue_iter(cur))) return rc;
+        cur = 1 - cur;
+      }
+    }
+    it += check;
+    for (int r = 0; r < nb; r++)
+      if (act[r]) its[r] += check;
+    if ((rc = sync_read(h, nb, s)) || (rc = timer_harvest(h, use_graph))) {
+      cleanup();
+      return rc;
+    }
+    bool update = false, changed = false;
+    for (int r = 0; r < nb; r++) {
+      if (!act[r]) continue;
+      const double rr = h->pinned[(size_t)r * kScal + S_RR], ww = h->pinned[(size_t)r * kScal + S_WW];
+      if (!std::isfinite(rr) || !std::isfinite(ww) || !(ww > 0.0)) {
+        act[r] = 0;
+        code[r] = DWF_ERR_BREAKDOWN;
+        changed = true;
+        continue;
+      }
+      const double rn = std::sqrt(rr);
+      if (rn < delta * rmax[r] || rn <= tol * bnorm[r] || it >= maxiter) update = true;
+    }
+    if (changed && (rc = push_active())) {
+      cleanup();
+      return rc;
+    }
+    if (update) {
+      // reliable update of every active right-hand side: x_hi += x_lo, r = b - D x_hi (FP64)
+      KLAUNCH(h, launch_accumulate64(h->g, W.x_hi, xprec, W.xlo, 1, nb, f64, fx, s, h->d_active));
+      if ((rc = apply_dbb(h, cv, P64, W.t64, W.x_hi, W.t64r, nb, nullptr, s))) {
+        cleanup();
+        return rc;
+      }
+      KLAUNCH(h, launch_sub64_norm(h->g, W.r_hi, W.b_hi, W.t64, nb, f64, &red_hi, s, h->d_active));
+      KLAUNCH(h, launch_convert(h->g, prec, W.r, P64, W.r_hi, nb, fi, f64, nullptr, s, h->d_active));
+      if ((rc = sync_read(h, nb, s))) {
+        cleanup();
+        return rc;
+      }
+      std::vector<int> restarted(nb, 0);
+      for (int r = 0; r < nb; r++) {
+        if (!act[r]) continue;
+        const double rrh = h->pinned[(size_t)r * kScal + S_RRHI];
+        true_res[r] = std::sqrt(rrh) / bnorm[r];
+        rmax[r] = std::sqrt(rrh);
+        rst[r]++;
+        if (true_res[r] <= tol) {
+          conv[r] = 1;
+          act[r] = 0;
+          t_done[r] = now_s();
+          continue;
+        }
+        // stagnation: three residual replacements in a row without a 10% gain
+        if (true_res[r] < 0.9 * best[r]) {
+          best[r] = true_res[r];
+          stalled[r] = 0;
+        } else if (++stalled[r] >= 3) {
+          act[r] = 0;
+          code[r] = DWF_ERR_NOT_CONVERGED;
+          t_done[r] = now_s();
+          continue;
+        }
+        if (restart) restarted[r] = 1;
+      }
+      if (restart && (rc = reset_beta(restarted))) {
+        cleanup();
+        return rc;
+      }
+      if ((rc = push_active())) {
+        cleanup();
+        return rc;
+      }
+    }
+    any_active = std::any_of(act.begin(), act.end(), [](int a) { return a != 0; });
+  }
+  cleanup();
+  int result = DWF_OK;
+  for (int r = 0; r < nb; r++) {
+    if (!conv[r] && !code[r]) code[r] = DWF_ERR_NOT_CONVERGED;
+    if (code[r] == DWF_ERR_BREAKDOWN) result = DWF_ERR_BREAKDOWN;
+    else if (code[r] && result == DWF_OK) result = code[r];
+    if (st) {
+      st[r].iterations = its[r];
+      st[r].restarts = rst[r];
+      st[r].true_resid = true_res[r];
+      st[r].applies = its[r];
+      st[r].applies_dag = its[r];
+      st[r].applies_fp64 = rst[r];
+      st[r].apply_ms = h->timed_ms[0];
+      st[r].apply_dag_ms = h->timed_ms[1];
+      st[r].kernel_launches = (int)(h->launches - launches0);
+      st[r].seconds = t_done[r] >= 0.0 ? t_done[r] : now_s();
+    }
+  }
+  if (result == DWF_ERR_BREAKDOWN) return fail(h, result, "CG breakdown (|Dp|^2 <= 0 or not finite)");
+  if (result)
+    return fail(h, result,
                 "CG did not reach the tolerance (maxiter reached or the true residual stagnated)");
   return DWF_OK;
 }
@@ -724,8 +897,8 @@ int cgnormal_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxit
   bool converged = false;
   const int check = std::max(1, h->opt.check_every);
   while (it < maxiter) {
-    if ((rc = apply_dbb(h, ms, prec, W.w, W.p, W.tr, 1, &red_ww, s))) return rc;
-    if ((rc = apply_dbb_dag(h, ms, prec, W.z, W.w, W.tr, W.tb, 1, nullptr, s))) return rc;
+    if ((rc = apply_dbb(h, view_of(ms), prec, W.w, W.p, W.tr, 1, &red_ww, s))) return rc;
+    if ((rc = apply_dbb_dag(h, view_of(ms), prec, W.z, W.w, W.tr, W.tb, 1, nullptr, s))) return rc;
     n_app++;
     n_dag++;
     const int nxt = 1 - cur;
@@ -743,8 +916,8 @@ int cgnormal_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxit
       const double rn = std::sqrt(rr);
       if (rn < delta * rmax || rn <= tol * bnorm || it >= maxiter) {
         KLAUNCH(h, launch_accumulate64(h->g, W.x_hi, xprec, W.xlo, 1, 1, f64, fx, s));
-        if ((rc = apply_dbb(h, ms, P64, W.t64, W.x_hi, W.t64r, 1, nullptr, s))) return rc;
-        if ((rc = apply_dbb_dag(h, ms, P64, t64b, W.t64, W.t64r, W.r_hi, 1, nullptr, s))) return rc;
+        if ((rc = apply_dbb(h, view_of(ms), P64, W.t64, W.x_hi, W.t64r, 1, nullptr, s))) return rc;
+        if ((rc = apply_dbb_dag(h, view_of(ms), P64, t64b, W.t64, W.t64r, W.r_hi, 1, nullptr, s))) return rc;
         n_64 += 2;
         KLAUNCH(h, launch_sub64_norm(h->g, W.r_hi, W.b_hi, t64b, 1, f64, &red_hi, s));
         KLAUNCH(h, launch_convert(h->g, prec, W.r, P64, W.r_hi, 1, fi, f64, &red_rr[nxt], s));
@@ -789,6 +962,95 @@ int solver_params(dwf_ctx* h, int* prec, double* delta, bool* restart) {
   return DWF_OK;
 }
 
+// Autotuner for the batched solve: times the batched D_bb apply of the inner
+// precision for every right-hand-side block size that fits in free device
+// memory, with direct and bulk-copy neighbour staging, and keeps the fastest
+// per right-hand side (within 3%, the larger block).  Results are cached per
+// (lattice, Ls, precision, nrhs) in the handle and, if DWF_AUTOTUNE_CACHE names
+// a file, there as "key nb staging" lines.
+int choose_rhs_block(dwf_ctx* h, int nrhs, int prec, cudaStream_t st, int* nb_out) {
+  if (h->opt.rhs_block > 0) {
+    *nb_out = std::min(h->opt.rhs_block, nrhs);
+    return DWF_OK;
+  }
+  if (nrhs == 1) {
+    *nb_out = 1;
+    return DWF_OK;
+  }
+  std::ostringstream key;
+  key << h->g.L[0] << "x" << h->g.L[1] << "x" << h->g.L[2] << "x" << h->g.L[3] << "_Ls" << h->g.Ls
+      << "_p" << prec << "_n" << nrhs;
+  auto it = h->tune.find(key.str());
+  const char* cache_file = std::getenv("DWF_AUTOTUNE_CACHE");
+  if (it == h->tune.end() && cache_file) {
+    std::ifstream in(cache_file);
+    std::string k;
+    int nb, tma;
+    while (in >> k >> nb >> tma)
+      if (k == key.str()) h->tune[k] = std::make_pair(nb, tma);
+    it = h->tune.find(key.str());
+  }
+  if (it != h->tune.end()) {
+    *nb_out = std::min(it->second.first, nrhs);
+    h->use_tma = it->second.second;
+    return DWF_OK;
+  }
+  size_t freeb = 0, totalb = 0;
+  CUCHK(h, cudaMemGetInfo(&freeb, &totalb));
+  const size_t per = solve_bytes_per_rhs(h->g, prec) + 3 * field_bytes(h->g, prec);
+  const double budget = 0.8 * (double)freeb;
+  const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+  std::vector<int> ok;
+  for (int c : cand)
+    if (c <= nrhs && (double)c * per <= budget) ok.push_back(c);
+  if (ok.empty()) ok.push_back(1);
+  const int maxnb = ok.back();
+  const size_t fi = field_bytes(h->g, prec);
+  void *x, *y, *t;
+  int rc;
+  if ((rc = get_ws(h, "tune_x", fi * maxnb, &x)) || (rc = get_ws(h, "tune_y", fi * maxnb, &y)) ||
+      (rc = get_ws(h, "tune_t", fi * maxnb, &t)))
+    return rc;
+  CUCHK(h, cudaMemsetAsync(x, 0, fi * maxnb, st));
+  MatSet* ms;
+  if ((rc = build_matset(h, h->alpha, h->m, &ms))) return rc;
+  cudaEvent_t e0, e1;
+  CUCHK(h, cudaEventCreate(&e0));
+  CUCHK(h, cudaEventCreate(&e1));
+  const int saved_tma = h->use_tma;
+  double best = 1e300;
+  int best_nb = 1, best_tma = saved_tma;
+  for (int nb : ok) {
+    for (int tma = 0; tma < 2; tma++) {
+      h->use_tma = tma;
+      if ((rc = apply_dbb(h, view_of(*ms), prec, y, x, t, nb, nullptr, st))) return rc;
+      CUCHK(h, cudaEventRecord(e0, st));
+      for (int k = 0; k < 3; k++)
+        if ((rc = apply_dbb(h, view_of(*ms), prec, y, x, t, nb, nullptr, st))) return rc;
+      CUCHK(h, cudaEventRecord(e1, st));
+      CUCHK(h, cudaEventSynchronize(e1));
+      float ms_t = 0.f;
+      CUCHK(h, cudaEventElapsedTime(&ms_t, e0, e1));
+      const double per_rhs = ms_t / (3.0 * nb);
+      if (per_rhs < 0.97 * best || (per_rhs <= best * 1.03 && nb > best_nb)) {
+        if (per_rhs < best) best = per_rhs;
+        best_nb = nb;
+        best_tma = tma;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->use_tma = best_tma;
+  h->tune[key.str()] = std::make_pair(best_nb, best_tma);
+  if (cache_file) {
+    std::ofstream out(cache_file, std::ios::app);
+    out << key.str() << " " << best_nb << " " << best_tma << "\n";
+  }
+  *nb_out = best_nb;
+  return DWF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -804,6 +1066,8 @@ int dwf_default_options(dwf_options* opt) {
   opt->solver = DWF_SOLVER_RELIABLE;
   opt->check_every = 16;
   opt->profile = 0;
+  opt->graph = 1;
+  opt->rhs_block = 0;
   return DWF_OK;
 }
 
@@ -849,6 +1113,11 @@ int dwf_create(dwf_handle* out, const int lattice[4], int Ls, double M5, double 
   // loads on the 16^3x32 workload; kept as an alternative staging strategy).
   h->use_tma = std::getenv("DWF_TMA") != nullptr;
   cudaGetDevice(&h->device);
+  if (cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(nullptr, DWF_ERR_CUDA, "stream creation failed");
+  }
   MatSet* ms;
   int rc = build_matset(h, alpha, m, &ms);
   if (!rc) rc = build_matset(h, 1.0, 1.0, &ms);
@@ -916,6 +1185,11 @@ int dwf_destroy(dwf_handle h) {
   if (h->nbr) cudaFree(h->nbr);
   if (h->dev_err) cudaFree(h->dev_err);
   for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+  if (h->cstream) cudaStreamDestroy(h->cstream);
+  if (h->d_active) {
+    cudaFree(h->d_active);
+    cudaFreeHost(h->pinned_i);
+  }
   if (h->scal) {
     cudaFree(h->scal);
     cudaFree(h->partial);
@@ -974,7 +1248,7 @@ int dwf_apply_Dbb(dwf_handle h, void* out, const void* in, int prec, int nrhs, d
   if (rc) return rc;
   void* tmp;
   if ((rc = get_ws(h, "apply_red_" + std::to_string(prec), field_bytes(h->g, prec) * nrhs, &tmp))) return rc;
-  return apply_dbb(h, *ms, prec, out, in, tmp, nrhs, nullptr, reinterpret_cast<cudaStream_t>(s));
+  return apply_dbb(h, view_of(*ms), prec, out, in, tmp, nrhs, nullptr, reinterpret_cast<cudaStream_t>(s));
 }
 
 int dwf_apply_Dbb_dag(dwf_handle h, void* out, const void* in, int prec, int nrhs, dwf_stream s) {
@@ -988,7 +1262,7 @@ int dwf_apply_Dbb_dag(dwf_handle h, void* out, const void* in, int prec, int nrh
   const size_t fb = field_bytes(h->g, prec) * nrhs;
   if ((rc = get_ws(h, "apply_red_" + std::to_string(prec), fb, &tr))) return rc;
   if ((rc = get_ws(h, "apply_blk_" + std::to_string(prec), fb, &tb))) return rc;
-  return apply_dbb_dag(h, *ms, prec, out, in, tr, tb, nrhs, nullptr, reinterpret_cast<cudaStream_t>(s));
+  return apply_dbb_dag(h, view_of(*ms), prec, out, in, tr, tb, nrhs, nullptr, reinterpret_cast<cudaStream_t>(s));
 }
 
 int dwf_apply_dalpha(dwf_handle h, double* out_full, const double* in_full, double alpha, double m,
@@ -1045,109 +1319,141 @@ int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* so
                    const double* alphas, dwf_stats* stats, dwf_stream s) {
   if (!h || !src4d || !prop4d || nrhs < 1) return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
   if (!h->gauge_loaded) return fail(h, DWF_ERR_STATE, "gauge field not loaded");
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  // all solver work runs on the handle's stream, after the caller's stream
+  CUCHK(h, cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(s)));
+  cudaStream_t st = h->cstream;
   const Geom& g = h->g;
   const size_t src_bytes = (size_t)g.Vh * 2 * 12 * 16;
   const bool host = !is_device_ptr(src4d);
   int rc;
-  if ((rc = ensure_reduce(h, nrhs))) return rc;
   int prec;
   double delta;
   bool restart;
   solver_params(h, &prec, &delta, &restart);
+  std::vector<MatSet*> ms(nrhs);
+  for (int k = 0; k < nrhs; k++)
+    if ((rc = build_matset(h, alphas ? alphas[k] : h->alpha, h->m, &ms[k]))) return rc;
+  MatSet* rhs_set;
+  if ((rc = build_matset(h, 1.0, 1.0, &rhs_set))) return rc;
+  int nb = 1;
+  if ((rc = choose_rhs_block(h, nrhs, prec, st, &nb))) return rc;
+  if ((rc = ensure_reduce(h, nb))) return rc;
   SolveWork W;
-  if ((rc = alloc_solve_work(h, prec, W))) return rc;
-  const size_t f64 = field_bytes(g, P64);
-  void *pb[2], *rhs[2], *psi_r, *src_d, *prop_d, *tmp5[2];
+  if ((rc = alloc_solve_work(h, prec, W, nb))) return rc;
+  const size_t f64 = field_bytes(g, P64), cnt = ms[0]->count();
+  void *pb[2], *rhs[2], *psi_r, *src_d = nullptr, *prop_d = nullptr, *tmp5[2], *bc64, *bc32;
   if ((rc = get_ws(h, "pb0", f64, &pb[0])) || (rc = get_ws(h, "pb1", f64, &pb[1])) ||
       (rc = get_ws(h, "rhs0", f64, &rhs[0])) || (rc = get_ws(h, "rhs1", f64, &rhs[1])) ||
       (rc = get_ws(h, "psi_r", f64, &psi_r)) || (rc = get_ws(h, "t5a", f64, &tmp5[0])) ||
-      (rc = get_ws(h, "t5b", f64, &tmp5[1])))
+      (rc = get_ws(h, "t5b", f64, &tmp5[1])) || (rc = get_ws(h, "bcoef64", cnt * 8 * nb, &bc64)) ||
+      (rc = get_ws(h, "bcoef32", cnt * 4 * nb, &bc32)))
     return rc;
   if (host) {
     if ((rc = get_ws(h, "src_d", src_bytes, &src_d)) || (rc = get_ws(h, "prop_d", src_bytes, &prop_d)))
       return rc;
   }
-  MatSet* rhs_set;
-  if ((rc = build_matset(h, 1.0, 1.0, &rhs_set))) return rc;
   const int black = h->opt.rb_parity, red = 1 - black;
-  int result = DWF_OK;
-  for (int k = 0; k < nrhs; k++) {
-    auto t0 = std::chrono::steady_clock::now();
-    const double alpha = alphas ? alphas[k] : h->alpha;
-    MatSet* ms;
-    if ((rc = build_matset(h, alpha, h->m, &ms))) return rc;
+  // rhs = D_1(1) P b for source k (full 5D, FP64) into rhs[0], rhs[1]
+  auto make_rhs = [&](int k) -> int {
     const double* src_k = src4d + (size_t)k * src_bytes / 8;
     if (host) {
       CUCHK(h, cudaMemcpyAsync(src_d, src_k, src_bytes, cudaMemcpyHostToDevice, st));
       src_k = reinterpret_cast<const double*>(src_d);
     }
-    // rhs = D_1(1) P b
     KLAUNCH(h, launch_source_pb(g, pb[0], pb[1], src_k, st));
     const void* pbc[2] = {pb[0], pb[1]};
-    if ((rc = apply_dalpha_halves(h, *rhs_set, rhs, pbc, st))) return rc;
-    // r'_b = I^-1 rhs_b + 1/2 I^-1 H_br (K rhs_r)
-    LocalLaunch Lk{};
-    Lk.prec = P64;
-    Lk.out = W.t64r;
-    Lk.in = rhs[red];
-    Lk.stride = f64;
-    Lk.nrhs = 1;
-    Lk.m = ms->ptr(P64, ms->mat_off(MatSet::K));
-    Lk.c = 1.0;
-    KLAUNCH(h, launch_local(g, Lk, st));
-    HopLaunch Hs = base_hop(h, P64, black, 1, f64);
-    Hs.out = W.b_hi;
-    Hs.v = W.t64r;
-    Hs.w = rhs[black];
-    Hs.post = ms->ptr(P64, ms->mat_off(MatSet::IINV));
-    Hs.loc = LOC_DENSE;
-    Hs.locm = ms->ptr(P64, ms->mat_off(MatSet::IINV));
-    Hs.c_hop = 0.5;
-    Hs.c_loc = 1.0;
-    KLAUNCH(h, launch_hop(g, Hs, st));
-    dwf_stats sk{};
-    const long long launches_k0 = h->launches;
-    rc = cgnr_solve(h, *ms, prec, h->opt.rel_tol, h->opt.maxiter, delta, restart, W, &sk, st);
-    if (rc && rc != DWF_ERR_NOT_CONVERGED) return rc;
+    return apply_dalpha_halves(h, *rhs_set, rhs, pbc, st);
+  };
+  int result = DWF_OK;
+  for (int blk = 0; blk < nrhs; blk += nb) {
+    const int n = std::min(nb, nrhs - blk);
+    auto t0 = std::chrono::steady_clock::now();
+    const long long l0 = h->launches;
+    for (int r = 0; r < n; r++) {
+      const MatSet& m = *ms[blk + r];
+      CUCHK(h, cudaMemcpyAsync(reinterpret_cast<char*>(bc64) + r * cnt * 8, m.dev[0], cnt * 8,
+                               cudaMemcpyDeviceToDevice, st));
+      CUCHK(h, cudaMemcpyAsync(reinterpret_cast<char*>(bc32) + r * cnt * 4, m.dev[1], cnt * 4,
+                               cudaMemcpyDeviceToDevice, st));
+      if ((rc = make_rhs(blk + r))) return rc;
+      // r'_b = I^-1 rhs_b + 1/2 I^-1 H_br (K rhs_r)
+      LocalLaunch Lk{};
+      Lk.prec = P64;
+      Lk.out = W.t64r;
+      Lk.in = rhs[red];
+      Lk.stride = f64;
+      Lk.nrhs = 1;
+      Lk.m = m.ptr(P64, m.mat_off(MatSet::K));
+      Lk.c = 1.0;
+      KLAUNCH(h, launch_local(g, Lk, st));
+      HopLaunch Hs = base_hop(h, P64, black, 1, f64);
+      Hs.out = reinterpret_cast<char*>(W.b_hi) + r * f64;
+      Hs.v = W.t64r;
+      Hs.w = rhs[black];
+      Hs.post = m.ptr(P64, m.mat_off(MatSet::IINV));
+      Hs.loc = LOC_DENSE;
+      Hs.locm = m.ptr(P64, m.mat_off(MatSet::IINV));
+      Hs.c_hop = 0.5;
+      Hs.c_loc = 1.0;
+      KLAUNCH(h, launch_hop(g, Hs, st));
+    }
+    std::vector<dwf_stats> sk(n);
+    CoefView cv{ms[blk], {bc64, bc32}, cnt, nullptr};
+    rc = cgnr_batched(h, cv, prec, h->opt.rel_tol, h->opt.maxiter, delta, restart, W, n, sk.data(), st);
+    if (rc && rc != DWF_ERR_NOT_CONVERGED && rc != DWF_ERR_BREAKDOWN) return rc;
     if (rc) result = rc;
-    // psi_r = I^-1 rhs_r + 1/2 I^-1 H_rb (B psi_b)
-    HopLaunch Hr = base_hop(h, P64, red, 1, f64);
-    Hr.out = psi_r;
-    Hr.v = W.x_hi;
-    Hr.w = rhs[red];
-    Hr.pre = PRE_B;
-    Hr.pre_diag = ms->ptr(P64, ms->bdiag_off());
-    Hr.pre_off = ms->ptr(P64, ms->boff_off());
-    Hr.post = ms->ptr(P64, ms->mat_off(MatSet::IINV));
-    Hr.loc = LOC_DENSE;
-    Hr.locm = ms->ptr(P64, ms->mat_off(MatSet::IINV));
-    Hr.c_hop = 0.5;
-    Hr.c_loc = 1.0;
-    KLAUNCH(h, launch_hop(g, Hr, st));
-    void* psi[2];
-    psi[black] = W.x_hi;
-    psi[red] = psi_r;
-    double* prop_k = prop4d + (size_t)k * src_bytes / 8;
-    KLAUNCH(h, launch_extract_z1(g, host ? reinterpret_cast<double*>(prop_d) : prop_k, psi[0], psi[1], st));
-    if (host) CUCHK(h, cudaMemcpyAsync(prop_k, prop_d, src_bytes, cudaMemcpyDeviceToHost, st));
-    if (sol5d) KLAUNCH(h, launch_merge_full(g, sol5d + (size_t)k * g.N5 * 2 * 24, psi[0], psi[1], st));
-    // full 5D residual |rhs - D_alpha psi| / |rhs|
-    const void* psic[2] = {psi[0], psi[1]};
-    if ((rc = apply_dalpha_halves(h, *ms, tmp5, psic, st))) return rc;
-    Reduce r0 = make_reduce(h, 0, S_T0), r1 = make_reduce(h, 1, S_T1);
-    Reduce n0 = make_reduce(h, 2, S_T2), n1 = make_reduce(h, 3, S_ZZ0);
-    KLAUNCH(h, launch_sub64_norm(g, tmp5[0], rhs[0], tmp5[0], 1, f64, &r0, st));
-    KLAUNCH(h, launch_sub64_norm(g, tmp5[1], rhs[1], tmp5[1], 1, f64, &r1, st));
-    KLAUNCH(h, launch_norm(g, P64, rhs[0], 1, f64, &n0, st));
-    KLAUNCH(h, launch_norm(g, P64, rhs[1], 1, f64, &n1, st));
-    if ((rc = sync_read(h, 1, st))) return rc;
-    sk.true_resid_5d = std::sqrt((h->pinned[S_T0] + h->pinned[S_T1]) / (h->pinned[S_T2] + h->pinned[S_ZZ0]));
-    sk.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    sk.kernel_launches = (int)(h->launches - launches_k0);
-    if (stats) stats[k] = sk;
+    for (int r = 0; r < n; r++) {
+      const int k = blk + r;
+      const MatSet& m = *ms[k];
+      void* xb = reinterpret_cast<char*>(W.x_hi) + r * f64;
+      if ((rc = make_rhs(k))) return rc;
+      // psi_r = I^-1 rhs_r + 1/2 I^-1 H_rb (B psi_b)
+      HopLaunch Hr = base_hop(h, P64, red, 1, f64);
+      Hr.out = psi_r;
+      Hr.v = xb;
+      Hr.w = rhs[red];
+      Hr.pre = PRE_B;
+      Hr.pre_diag = m.ptr(P64, m.bdiag_off());
+      Hr.pre_off = m.ptr(P64, m.boff_off());
+      Hr.post = m.ptr(P64, m.mat_off(MatSet::IINV));
+      Hr.loc = LOC_DENSE;
+      Hr.locm = m.ptr(P64, m.mat_off(MatSet::IINV));
+      Hr.c_hop = 0.5;
+      Hr.c_loc = 1.0;
+      KLAUNCH(h, launch_hop(g, Hr, st));
+      void* psi[2];
+      psi[black] = xb;
+      psi[red] = psi_r;
+      double* prop_k = prop4d + (size_t)k * src_bytes / 8;
+      KLAUNCH(h, launch_extract_z1(g, host ? reinterpret_cast<double*>(prop_d) : prop_k, psi[0],
+                                   psi[1], st));
+      if (host) CUCHK(h, cudaMemcpyAsync(prop_k, prop_d, src_bytes, cudaMemcpyDeviceToHost, st));
+      if (sol5d) KLAUNCH(h, launch_merge_full(g, sol5d + (size_t)k * g.N5 * 2 * 24, psi[0], psi[1], st));
+      // full 5D residual |rhs - D_alpha psi| / |rhs|
+      const void* psic[2] = {psi[0], psi[1]};
+      if ((rc = apply_dalpha_halves(h, m, tmp5, psic, st))) return rc;
+      Reduce r0 = make_reduce(h, 0, S_T0), r1 = make_reduce(h, 1, S_T1);
+      Reduce n0 = make_reduce(h, 2, S_T2), n1 = make_reduce(h, 3, S_ZZ0);
+      KLAUNCH(h, launch_sub64_norm(g, tmp5[0], rhs[0], tmp5[0], 1, f64, &r0, st));
+      KLAUNCH(h, launch_sub64_norm(g, tmp5[1], rhs[1], tmp5[1], 1, f64, &r1, st));
+      KLAUNCH(h, launch_norm(g, P64, rhs[0], 1, f64, &n0, st));
+      KLAUNCH(h, launch_norm(g, P64, rhs[1], 1, f64, &n1, st));
+      if ((rc = sync_read(h, 1, st))) return rc;
+      sk[r].true_resid_5d =
+          std::sqrt((h->pinned[S_T0] + h->pinned[S_T1]) / (h->pinned[S_T2] + h->pinned[S_ZZ0]));
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    (void)secs;
+    for (int r = 0; r < n; r++) {
+      sk[r].kernel_launches = (int)(h->launches - l0);
+      if (stats) stats[blk + r] = sk[r];
+    }
   }
-  return result;
+  CUCHK(h, cudaStreamSynchronize(st));
+  if (result == DWF_ERR_NOT_CONVERGED)
+    return fail(h, result, "CG did not reach the tolerance for at least one source");
+  if (result == DWF_ERR_BREAKDOWN) return fail(h, result, "CG breakdown for at least one source");
+  return DWF_OK;
 }
 
 int dwf_force(dwf_handle h, double* dSdU, const double* phi_half, const double* X_half,
@@ -1188,7 +1494,7 @@ int dwf_force(dwf_handle h, double* dSdU, const double* phi_half, const double* 
     tred = W.t64r;
   }
   // Y = D_bb X
-  if ((rc = apply_dbb(h, *ms, P64, Y, X, tred, 1, nullptr, st))) return rc;
+  if ((rc = apply_dbb(h, view_of(*ms), P64, Y, X, tred, 1, nullptr, st))) return rc;
   // eta1 = I^-T Y
   LocalLaunch Le{};
   Le.prec = P64;
@@ -1249,7 +1555,7 @@ int apply_dbb_with_scratch(dwf_handle h, void* out, const void* in, int prec, in
                     "-byte static scratch buffer; use dwf_apply_Dbb");
   auto it = h->mats.find(std::make_pair(h->alpha, h->m));
   if (it == h->mats.end()) return fail(h, DWF_ERR_STATE, "operator matrices missing");
-  return apply_dbb(h, it->second, prec, out, in, scratch, nrhs, nullptr, s);
+  return apply_dbb(h, view_of(it->second), prec, out, in, scratch, nrhs, nullptr, s);
 }
 
 }  // namespace dwf

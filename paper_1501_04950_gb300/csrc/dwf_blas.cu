@@ -226,10 +226,11 @@ __global__ void extract_z1_kernel(const Geom g, double* prop, const void* p0, co
 template <class SPX, class SP>
 __global__ void __launch_bounds__(kBlasThreads) xr_update_kernel(
     const Geom g, void* x, void* r, const void* p, const void* w, const double* num,
-    const double* den, int sstride, size_t stride_x, size_t stride, Reduce red) {
+    const double* den, int sstride, size_t stride_x, size_t stride, Reduce red, const int* active) {
   using T = typename SP::T;
   using TX = typename SPX::T;
   const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
   const size_t off = rhs * stride, offx = rhs * stride_x;
   const double ad = num[rhs * sstride] / den[rhs * sstride];
   const T a = (T)ad;
@@ -257,9 +258,10 @@ __global__ void __launch_bounds__(kBlasThreads) xr_update_kernel(
 template <class SP>
 __global__ void __launch_bounds__(kBlasThreads) p_update_kernel(
     const Geom g, void* p, const void* z, const double* num, const double* den, int sstride,
-    size_t stride) {
+    size_t stride, const int* active) {
   using T = typename SP::T;
   const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
   const size_t off = rhs * stride;
   const T beta = (T)(num[rhs * sstride] / den[rhs * sstride]);
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
@@ -275,10 +277,12 @@ __global__ void __launch_bounds__(kBlasThreads) p_update_kernel(
 
 template <class SPD, class SPS>
 __global__ void __launch_bounds__(kBlasThreads) convert_kernel(
-    const Geom g, void* dst, const void* src, size_t sd, size_t ss, Reduce red, int do_norm) {
+    const Geom g, void* dst, const void* src, size_t sd, size_t ss, Reduce red, int do_norm,
+    const int* active) {
   using TD = typename SPD::T;
   using TS = typename SPS::T;
   const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
   double acc = 0.0;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
     Spinor<TS> a;
@@ -297,9 +301,10 @@ __global__ void __launch_bounds__(kBlasThreads) convert_kernel(
 
 template <class SPS>
 __global__ void __launch_bounds__(kBlasThreads) accumulate64_kernel(
-    const Geom g, void* x64, void* src, int zero_src, size_t sd, size_t ss) {
+    const Geom g, void* x64, void* src, int zero_src, size_t sd, size_t ss, const int* active) {
   using TS = typename SPS::T;
   const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
     Spinor<TS> a;
     SPS::load(reinterpret_cast<const char*>(src) + rhs * ss, n, g.N5, a);
@@ -318,8 +323,10 @@ __global__ void __launch_bounds__(kBlasThreads) accumulate64_kernel(
 }
 
 __global__ void __launch_bounds__(kBlasThreads) sub64_norm_kernel(
-    const Geom g, void* out, const void* a, const void* b, size_t stride, Reduce red) {
+    const Geom g, void* out, const void* a, const void* b, size_t stride, Reduce red,
+    const int* active) {
   const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
   const size_t off = rhs * stride;
   double acc = 0.0;
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
@@ -439,12 +446,12 @@ cudaError_t launch_extract_z1(const Geom& g, double* prop, const void* p0, const
 cudaError_t launch_xr_update(const Geom& g, int prec, int xprec, void* x, void* r, const void* p,
                              const void* w, const double* num, const double* den, int sstride,
                              int nrhs, size_t stride_x, size_t stride, const Reduce* red,
-                             cudaStream_t s) {
+                             cudaStream_t s, const int* active) {
   dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
   if (xprec == prec) {
-    DWF_PREC_SWITCH(prec, SP, xr_update_kernel<SP, SP><<<grid, kBlasThreads, 0, s>>>(g, x, r, p, w, num, den, sstride, stride_x, stride, *red));
+    DWF_PREC_SWITCH(prec, SP, xr_update_kernel<SP, SP><<<grid, kBlasThreads, 0, s>>>(g, x, r, p, w, num, den, sstride, stride_x, stride, *red, active));
   } else if (xprec == P32) {
-    DWF_PREC_SWITCH(prec, SP, xr_update_kernel<Store32, SP><<<grid, kBlasThreads, 0, s>>>(g, x, r, p, w, num, den, sstride, stride_x, stride, *red));
+    DWF_PREC_SWITCH(prec, SP, xr_update_kernel<Store32, SP><<<grid, kBlasThreads, 0, s>>>(g, x, r, p, w, num, den, sstride, stride_x, stride, *red, active));
   } else {
     return cudaErrorInvalidValue;
   }
@@ -453,45 +460,46 @@ cudaError_t launch_xr_update(const Geom& g, int prec, int xprec, void* x, void* 
 
 cudaError_t launch_p_update(const Geom& g, int prec, void* p, const void* z, const double* num,
                             const double* den, int sstride, int nrhs, size_t stride,
-                            cudaStream_t s) {
+                            cudaStream_t s, const int* active) {
   dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
-  DWF_PREC_SWITCH(prec, SP, p_update_kernel<SP><<<grid, kBlasThreads, 0, s>>>(g, p, z, num, den, sstride, stride));
+  DWF_PREC_SWITCH(prec, SP, p_update_kernel<SP><<<grid, kBlasThreads, 0, s>>>(g, p, z, num, den, sstride, stride, active));
   return cudaGetLastError();
 }
 
 template <class SPD>
 cudaError_t convert_from(const Geom& g, void* dst, int prec_s, const void* src, int nrhs, size_t sd,
-                         size_t ss, const Reduce* red, cudaStream_t s) {
+                         size_t ss, const Reduce* red, cudaStream_t s, const int* active) {
   dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
   Reduce r{};
   if (red) r = *red;
   const int dn = red != nullptr;
-  DWF_PREC_SWITCH(prec_s, SPS, convert_kernel<SPD, SPS><<<grid, kBlasThreads, 0, s>>>(g, dst, src, sd, ss, r, dn));
+  DWF_PREC_SWITCH(prec_s, SPS, convert_kernel<SPD, SPS><<<grid, kBlasThreads, 0, s>>>(g, dst, src, sd, ss, r, dn, active));
   return cudaGetLastError();
 }
 
 cudaError_t launch_convert(const Geom& g, int prec_d, void* dst, int prec_s, const void* src,
-                           int nrhs, size_t sd, size_t ss, const Reduce* red, cudaStream_t s) {
+                           int nrhs, size_t sd, size_t ss, const Reduce* red, cudaStream_t s,
+                           const int* active) {
   switch (prec_d) {
-    case P64: return convert_from<Store64>(g, dst, prec_s, src, nrhs, sd, ss, red, s);
-    case P32: return convert_from<Store32>(g, dst, prec_s, src, nrhs, sd, ss, red, s);
-    case P16: return convert_from<Store16<false>>(g, dst, prec_s, src, nrhs, sd, ss, red, s);
-    case PB16: return convert_from<Store16<true>>(g, dst, prec_s, src, nrhs, sd, ss, red, s);
+    case P64: return convert_from<Store64>(g, dst, prec_s, src, nrhs, sd, ss, red, s, active);
+    case P32: return convert_from<Store32>(g, dst, prec_s, src, nrhs, sd, ss, red, s, active);
+    case P16: return convert_from<Store16<false>>(g, dst, prec_s, src, nrhs, sd, ss, red, s, active);
+    case PB16: return convert_from<Store16<true>>(g, dst, prec_s, src, nrhs, sd, ss, red, s, active);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_accumulate64(const Geom& g, void* x64, int prec_s, void* src, int zero_src,
-                                int nrhs, size_t sd, size_t ss, cudaStream_t s) {
+                                int nrhs, size_t sd, size_t ss, cudaStream_t s, const int* active) {
   dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
-  DWF_PREC_SWITCH(prec_s, SPS, accumulate64_kernel<SPS><<<grid, kBlasThreads, 0, s>>>(g, x64, src, zero_src, sd, ss));
+  DWF_PREC_SWITCH(prec_s, SPS, accumulate64_kernel<SPS><<<grid, kBlasThreads, 0, s>>>(g, x64, src, zero_src, sd, ss, active));
   return cudaGetLastError();
 }
 
 cudaError_t launch_sub64_norm(const Geom& g, void* out, const void* a, const void* b, int nrhs,
-                              size_t stride, const Reduce* red, cudaStream_t s) {
+                              size_t stride, const Reduce* red, cudaStream_t s, const int* active) {
   dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
-  sub64_norm_kernel<<<grid, kBlasThreads, 0, s>>>(g, out, a, b, stride, *red);
+  sub64_norm_kernel<<<grid, kBlasThreads, 0, s>>>(g, out, a, b, stride, *red, active);
   return cudaGetLastError();
 }
 

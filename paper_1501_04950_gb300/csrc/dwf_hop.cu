@@ -72,6 +72,8 @@ struct HopArgs {
   T c_hop, c_loc;
   int p;
   Reduce red;
+  size_t cstride;
+  const int* active;
 };
 
 template <class SP, class GP, int PRE, int MU, int DIR>
@@ -172,9 +174,11 @@ __global__ void __launch_bounds__(256) hop_kernel(const Geom g, const HopArgs<ty
   const int h = blockIdx.x * blockDim.y + j;
   const bool active = h < g.Vh;
   const int rhs = blockIdx.z;
+  if (a.active && !a.active[rhs]) return;
+  const size_t co = (size_t)rhs * a.cstride;
 
-  if (POST) load_matrix_T(smat, a.post, Ls, tid, nth);
-  if (LOC == LOC_DENSE) load_matrix_T(smat_loc, a.locm, Ls, tid, nth);
+  if (POST) load_matrix_T(smat, a.post + co, Ls, tid, nth);
+  if (LOC == LOC_DENSE) load_matrix_T(smat_loc, a.locm + co, Ls, tid, nth);
   if (POST || LOC == LOC_DENSE) __syncthreads();
 
   const char* vb = reinterpret_cast<const char*>(a.v) + rhs * a.stride;
@@ -186,10 +190,10 @@ __global__ void __launch_bounds__(256) hop_kernel(const Geom g, const HopArgs<ty
     const Coords c = site_coords(g, h, a.p);
     T bd[2] = {0, 0}, bo[2] = {0, 0};
     if (PRE == PRE_B) {
-      bd[0] = a.pre_diag[s];
-      bd[1] = a.pre_diag[Ls + s];
-      bo[0] = a.pre_off[s];
-      bo[1] = a.pre_off[Ls + s];
+      bd[0] = a.pre_diag[co + s];
+      bd[1] = a.pre_diag[co + Ls + s];
+      bo[0] = a.pre_off[co + s];
+      bo[1] = a.pre_off[co + Ls + s];
     }
     const int sp = s == 0 ? Ls - 1 : s - 1;
     const int sn = s == Ls - 1 ? 0 : s + 1;
@@ -254,7 +258,8 @@ template <class SP>
 __global__ void __launch_bounds__(256) local_kernel(const Geom g, void* out, const void* in,
                                                     size_t stride, const typename SP::T* m,
                                                     typename SP::T c, int g5in, Reduce red,
-                                                    int do_norm) {
+                                                    int do_norm, size_t cstride,
+                                                    const int* rhs_on) {
   using T = typename SP::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* smat = reinterpret_cast<T*>(smem_raw);
@@ -266,8 +271,9 @@ __global__ void __launch_bounds__(256) local_kernel(const Geom g, void* out, con
   const int h = blockIdx.x * blockDim.y + j;
   const bool active = h < g.Vh;
   const int rhs = blockIdx.z;
+  if (rhs_on && !rhs_on[rhs]) return;
   const size_t off = rhs * stride;
-  load_matrix_T(smat, m, Ls, tid, nth);
+  load_matrix_T(smat, m + (size_t)rhs * cstride, Ls, tid, nth);
   Spinor<T> x;
 #pragma unroll
   for (int k = 0; k < 12; k++) x.c[k] = cmake<T>(0, 0);
@@ -321,6 +327,8 @@ cudaError_t run_hop(const Geom& g, const HopLaunch& L, cudaStream_t st) {
   a.c_hop = (T)L.c_hop;
   a.c_loc = (T)L.c_loc;
   a.p = L.p;
+  a.cstride = L.cstride;
+  a.active = L.active;
   if (L.red) a.red = *L.red;
   const int S = L.block_sites > 0 ? L.block_sites : default_block_sites(L.prec, g.Ls);
   const size_t smem = hop_smem(L.prec, g.Ls, S);
@@ -382,7 +390,7 @@ cudaError_t run_local(const Geom& g, const LocalLaunch& L, cudaStream_t st) {
   dim3 block(g.Ls, S, 1);
   dim3 grid((g.Vh + S - 1) / S, 1, L.nrhs);
   k<<<grid, block, smem, st>>>(g, L.out, L.in, L.stride, reinterpret_cast<const T*>(L.m), (T)L.c,
-                               L.g5in, red, L.red != nullptr);
+                               L.g5in, red, L.red != nullptr, L.cstride, L.active);
   return cudaGetLastError();
 }
 

@@ -70,6 +70,8 @@ struct Args {
   T c_hop, c_loc;
   Reduce red;
   int* err;             // set to 1 when a bounded wait gives up (TMA path)
+  size_t cstride;       // elements between right-hand sides of bdiag, boff, chain
+  const int* active;    // per right-hand side: 0 skips it (nullptr: all active)
 };
 
 // h_k = cp1 P_k + cp2 P'_k - SG phi_k (cm1 M_pi(k) + cm2 M'_pi(k)), with
@@ -408,10 +410,12 @@ __global__ void __launch_bounds__(128, MINB)
   const int h = blockIdx.x * blockDim.y + j;
   const bool active = h < g.Vh;
   const int rhs = blockIdx.z;
+  if (a.active && !a.active[rhs]) return;
+  const size_t co = (size_t)rhs * a.cstride;
   const int s0 = 2 * t;
   constexpr bool kChain = POST != PR_NONE || LOCP != PR_NONE;
   if (kChain) {
-    for (int i = tid; i < chain_block(LS); i += nth) coef[i] = a.chain[i];
+    for (int i = tid; i < chain_block(LS); i += nth) coef[i] = a.chain[co + i];
   }
   const char* vb = reinterpret_cast<const char*>(a.v) + rhs * a.stride;
   Spinor<T> acc0, acc1;
@@ -428,8 +432,8 @@ __global__ void __launch_bounds__(128, MINB)
       for (int ch = 0; ch < 2; ch++)
 #pragma unroll
         for (int k = 0; k < 2; k++) {
-          bd[ch][k] = __ldg(a.bdiag + ch * LS + s0 + k);
-          bo[ch][k] = __ldg(a.boff + ch * LS + s0 + k);
+          bd[ch][k] = __ldg(a.bdiag + co + ch * LS + s0 + k);
+          bo[ch][k] = __ldg(a.boff + co + ch * LS + s0 + k);
         }
     }
     const int sm = s0 == 0 ? LS - 1 : s0 - 1;
@@ -655,6 +659,8 @@ __global__ void __launch_bounds__(128, 4)
   const int h = blockIdx.x * S + j;
   const bool active = h < g.Vh;
   const int rhs = blockIdx.z;
+  if (a.active && !a.active[rhs]) return;
+  const size_t co = (size_t)rhs * a.cstride;
   const int s0 = 2 * t;
   // [mbar 2][coef][stage 0][stage 1]; the chain buffer aliases the stages
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw);
@@ -670,7 +676,7 @@ __global__ void __launch_bounds__(128, 4)
   }
   constexpr bool kChain = POST != PR_NONE || LOCP != PR_NONE;
   if (kChain) {
-    for (int i = tid; i < chain_block(LS); i += nth) coef[i] = a.chain[i];
+    for (int i = tid; i < chain_block(LS); i += nth) coef[i] = a.chain[co + i];
   }
   int nb[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   T bd[2][2] = {{0, 0}, {0, 0}}, bo[2][2] = {{0, 0}, {0, 0}};
@@ -683,8 +689,8 @@ __global__ void __launch_bounds__(128, 4)
       for (int ch = 0; ch < 2; ch++)
 #pragma unroll
         for (int k = 0; k < 2; k++) {
-          bd[ch][k] = __ldg(a.bdiag + ch * LS + s0 + k);
-          bo[ch][k] = __ldg(a.boff + ch * LS + s0 + k);
+          bd[ch][k] = __ldg(a.bdiag + co + ch * LS + s0 + k);
+          bo[ch][k] = __ldg(a.boff + co + ch * LS + s0 + k);
         }
     }
   }
@@ -742,7 +748,8 @@ template <class SP, int LS, int PROG>
 __global__ void __launch_bounds__(128) local_kernel(const Geom g, void* out, const void* in,
                                                     size_t stride, const typename SP::T* chain,
                                                     typename SP::T c, int g5in, Reduce red,
-                                                    int do_norm) {
+                                                    int do_norm, size_t cstride,
+                                                    const int* rhs_on) {
   using T = typename SP::T;
   constexpr int SST = site_stride(LS);
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -753,8 +760,9 @@ __global__ void __launch_bounds__(128) local_kernel(const Geom g, void* out, con
   const int h = blockIdx.x * blockDim.y + j;
   const bool active = h < g.Vh;
   const int rhs = blockIdx.z;
+  if (rhs_on && !rhs_on[rhs]) return;
   const int s0 = 2 * t;
-  for (int i = tid; i < chain_block(LS); i += nth) coef[i] = chain[i];
+  for (int i = tid; i < chain_block(LS); i += nth) coef[i] = chain[(size_t)rhs * cstride + i];
   const size_t off = rhs * stride;
   const int n = h * LS + t, n1 = n + LS / 2;
   Spinor<T> x0, x1;
@@ -823,6 +831,8 @@ cudaError_t run(const Geom& g, const HopLaunch& L, cudaStream_t st) {
   a.c_loc = (T)L.c_loc;
   if (L.red) a.red = *L.red;
   a.err = L.err;
+  a.cstride = L.cstride;
+  a.active = L.active;
   const int S = block_sites(LS);
   dim3 block(LS / 2, S, 1);
   dim3 grid((g.Vh + S - 1) / S, 1, L.nrhs);
@@ -890,7 +900,7 @@ cudaError_t run_local(const Geom& g, const LocalLaunch& L, cudaStream_t st) {
   dim3 block(LS / 2, S, 1);
   dim3 grid((g.Vh + S - 1) / S, 1, L.nrhs);
   k<<<grid, block, smem, st>>>(g, L.out, L.in, L.stride, reinterpret_cast<const T*>(L.chain),
-                               (T)L.c, L.g5in, red, L.red != nullptr);
+                               (T)L.c, L.g5in, red, L.red != nullptr, L.cstride, L.active);
   return cudaGetLastError();
 }
 

@@ -87,6 +87,9 @@ struct HopLaunch {
   const int* nbr;           // [2 parities][Vh][8] neighbour half indices, bit 31 = sign
   int* err;                 // device flag set when a bounded wait gives up
   int use_tma;              // 1: stage neighbours through shared memory with bulk copies
+  size_t cstride;           // elements between right-hand sides of every coefficient
+                            // array (pre_diag, pre_off, post, locm, chain); 0: shared
+  const int* active;        // per right-hand side: 0 skips it (nullptr: all active)
 };
 // Tries the tuned kernel first, then the generic one.
 cudaError_t launch_hop(const Geom& g, const HopLaunch& a, cudaStream_t s);
@@ -109,6 +112,8 @@ struct LocalLaunch {
   const Reduce* red;
   int prog;                 // hop2::PR_* equivalent of m (tuned path)
   const void* chain;
+  size_t cstride;           // elements between right-hand sides of m / chain (0: shared)
+  const int* active;
 };
 cudaError_t launch_local(const Geom& g, const LocalLaunch& a, cudaStream_t s);
 cudaError_t launch_hop2_f64_local(const Geom& g, const LocalLaunch& a, cudaStream_t s);
@@ -146,21 +151,23 @@ cudaError_t launch_extract_z1(const Geom& g, double* prop4d, const void* par0, c
 cudaError_t launch_xr_update(const Geom& g, int prec, int xprec, void* x, void* r, const void* p,
                              const void* w, const double* num, const double* den, int sstride,
                              int nrhs, size_t stride_x, size_t stride, const Reduce* red,
-                             cudaStream_t s);
+                             cudaStream_t s, const int* active = nullptr);
 // p = z + beta p, beta = num / den.
 cudaError_t launch_p_update(const Geom& g, int prec, void* p, const void* z, const double* num,
                             const double* den, int sstride, int nrhs, size_t stride,
-                            cudaStream_t s);
+                            cudaStream_t s, const int* active = nullptr);
 // dst (prec_d) = src (prec_s), optional |dst|^2 (of the converted values).
 cudaError_t launch_convert(const Geom& g, int prec_d, void* dst, int prec_s, const void* src,
                            int nrhs, size_t stride_d, size_t stride_s, const Reduce* red,
-                           cudaStream_t s);
+                           cudaStream_t s, const int* active = nullptr);
 // x64 += src (prec_s); then src = 0 if zero_src.
 cudaError_t launch_accumulate64(const Geom& g, void* x64, int prec_s, void* src, int zero_src,
-                                int nrhs, size_t stride_d, size_t stride_s, cudaStream_t s);
+                                int nrhs, size_t stride_d, size_t stride_s, cudaStream_t s,
+                                const int* active = nullptr);
 // out = a - b (FP64), |out|^2 -> red.
 cudaError_t launch_sub64_norm(const Geom& g, void* out, const void* a, const void* b, int nrhs,
-                              size_t stride, const Reduce* red, cudaStream_t s);
+                              size_t stride, const Reduce* red, cudaStream_t s,
+                              const int* active = nullptr);
 // |x|^2 -> red.
 cudaError_t launch_norm(const Geom& g, int prec, const void* x, int nrhs, size_t stride,
                         const Reduce* red, cudaStream_t s);

@@ -29,7 +29,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision_inner", ctypes.c_int), ("rb_parity", ctypes.c_int),
                 ("bc_t", ctypes.c_int), ("rel_tol", ctypes.c_double), ("maxiter", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("solver", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("profile", ctypes.c_int),
+                ("graph", ctypes.c_int), ("rhs_block", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
