@@ -218,6 +218,49 @@ def run_apply_only(args):
     print(json.dumps(res), flush=True)
 
 
+def run_batched(args):
+    """Batched propagator solves: 12 point sources x alpha in {1, 1.5} in one call per lattice.
+
+    Reports, per lattice, solves per second and the per-solve latency (time from the
+    start of its batch to its convergence) p50 / p99, for the FP32-inner solver
+    (autotuned right-hand-side block) and the plain FP64 GPU CG.
+    """
+    import torch
+    from paper_1501_04950_gb300 import dwf
+    from synthetic import gauge_field, point_source4d
+    dev = torch.device("cuda", 0)
+    out = []
+    for lat in args.batched.split(","):
+        L = tuple(int(v) for v in lat.split("x"))
+        U = torch.from_numpy(gauge_field(L, EPS, seed=0)).to(dev)
+        srcs = [point_source4d(L, sp, c) for sp in range(4) for c in range(3)]
+        src = torch.from_numpy(np.stack(srcs + srcs)).to(dev)
+        alphas = [1.0] * 12 + [1.5] * 12
+        prop = torch.empty_like(src)
+        row = {"lattice": lat, "Ls": LS, "nrhs": 24}
+        for name, opts in [("mixed_fp32", {}), ("mixed_fp16", {"precision_inner": dwf.FP16})]:
+            op = dwf.DWF(L, LS, M5, MASS, 1.0, np.full(LS, B), np.full(LS, C), **opts)
+            op.load_gauge(U)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = op.cgne_solve(src, prop, nrhs=24, alphas=alphas, allow_not_converged=True)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            lat_s = sorted(x["seconds"] for x in st)
+            row[name] = {
+                "seconds": dt, "solves_per_s": 24 / dt,
+                "latency_p50_s": float(np.percentile(lat_s, 50)),
+                "latency_p99_s": float(np.percentile(lat_s, 99)),
+                "iterations_alpha1": int(np.mean([x["iterations"] for x in st[:12]])),
+                "iterations_alpha1.5": int(np.mean([x["iterations"] for x in st[12:]])),
+                "max_true_resid": max(x["true_resid"] for x in st),
+            }
+            op.close()
+        out.append(row)
+        print(json.dumps(row), flush=True)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -228,10 +271,14 @@ def main():
     ap.add_argument("--inner", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the alpha sweep")
     ap.add_argument("--apply-only", type=int, default=0,
                     help="run this many D_bb and D_bb^+ applies of the workload and report their "
                          "CUDA-event times (the case the ncu captures use)")
     ap.add_argument("--lattice", default=None, help="override Lx,Ly,Lz,Lt (apply-only mode)")
+    ap.add_argument("--batched", default=None,
+                    help="batched mode: comma-separated lattices such as 8x8x8x8,16x16x16x32; "
+                         "12 spin-colour point sources x alpha in {1, 1.5} per lattice")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -244,6 +291,9 @@ def main():
         return
     if args.apply_only:
         run_apply_only(args)
+        return
+    if args.batched:
+        run_batched(args)
         return
 
     import torch
@@ -337,6 +387,29 @@ def main():
                 "true_resid": s64["true_resid"]}
         op64.close()
 
+    sweep = None
+    if not args.no_sweep:
+        # config-2 alpha sweep: one batched call per solver, the same source for every alpha
+        alphas = [0.5, 0.75, 1.0, 1.25, 1.5, 2.0]
+        src6 = src.unsqueeze(0).repeat(len(alphas), *([1] * src.dim())).contiguous()
+        prop6 = torch.empty_like(src6)
+        sweep = {"alphas": alphas}
+        for name, opts in [("mixed_fp32", {}), ("fp64", {"solver": dwf.SOLVER_FP64})]:
+            ops = dwf.DWF(LATTICE, LS, M5, MASS, 1.0, np.full(LS, B), np.full(LS, C),
+                          rhs_block=len(alphas), **opts)
+            ops.load_gauge(U)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st6 = ops.cgne_solve(src6, prop6, nrhs=len(alphas), alphas=alphas)
+            torch.cuda.synchronize()
+            sweep[name] = {"batch_seconds": time.perf_counter() - t0,
+                           "iterations": [x["iterations"] for x in st6],
+                           "seconds_to_converge": [round(x["seconds"], 4) for x in st6],
+                           "true_resid": [x["true_resid"] for x in st6]}
+            ops.close()
+        it1 = sweep["mixed_fp32"]["iterations"][2]
+        sweep["relative_iterations"] = [round(x / it1, 4) for x in sweep["mixed_fp32"]["iterations"]]
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         gbs, times = oracle_apply_sample(3)
@@ -364,6 +437,7 @@ def main():
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                          "peak_kind": peak_kind, "traffic": measured_traffic(),
                          "bytes_per_apply": b_inner},
+            "alpha_sweep": sweep,
             "cpu_baseline": cpu,
             "e2e": {"value": moved_e2e * world / dt_e2e / 1e9, "unit": "GB/s",
                     "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},

@@ -165,6 +165,7 @@ __device__ __forceinline__ void hop_dir(const Geom& g, int nb, int h, int s0, in
   reconstruct_add<T, MU, DIR>(acc1, c0, c1);
 }
 
+
 // Lower-form cyclic bidiagonal multiply: y_k = a_k v_k + b_k v_{k-1 mod L}.
 template <typename T, int LS, int CPT>
 __device__ __forceinline__ void chain_mult(T (&V)[CPT][LS], const T* c) {
