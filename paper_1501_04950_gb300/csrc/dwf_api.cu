@@ -203,6 +203,7 @@ struct dwf_ctx {
   int* nbr = nullptr;                            // [2][Vh][8] neighbour table
   int* dev_err = nullptr;                        // set by a kernel whose bounded wait gave up
   int use_tma = 0;                               // DWF_TMA: bulk-copy staged tuned kernels
+  int check = 16;                                // effective iterations between polls
   bool gauge_loaded = false;
   std::vector<void*> allocs;
   // workspace
@@ -707,7 +708,7 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
                                 &red_rr, s, h->d_active));
     return DWF_OK;
   };
-  int check = std::max(2, h->opt.check_every);
+  int check = std::max(2, h->check);
   if (check & 1) check++;
   const bool use_graph = h->opt.graph != 0;
   cudaGraph_t graph = nullptr;
@@ -895,7 +896,7 @@ int cgnormal_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxit
   double rmax = bnorm, true_res = 1.0, best_res = 1.0;
   int it = 0, restarts = 0, stalled = 0;
   bool converged = false;
-  const int check = std::max(1, h->opt.check_every);
+  const int check = std::max(1, h->check);
   while (it < maxiter) {
     if ((rc = apply_dbb(h, view_of(ms), prec, W.w, W.p, W.tr, 1, &red_ww, s))) return rc;
     if ((rc = apply_dbb_dag(h, view_of(ms), prec, W.z, W.w, W.tr, W.tb, 1, nullptr, s))) return rc;
@@ -949,9 +950,15 @@ int cgnormal_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxit
   return DWF_OK;
 }
 
+// Effective solver settings.  reliable_delta <= 0 and check_every <= 0 select
+// precision-dependent defaults: 16-bit inner fields drift from the true residual
+// within a few iterations, so they replace it more often (delta 0.3, poll every
+// 4 iterations) than FP32 (0.1, every 16).
 int solver_params(dwf_ctx* h, int* prec, double* delta, bool* restart) {
   *prec = h->opt.precision_inner;
-  *delta = h->opt.reliable_delta;
+  const bool half = *prec == P16 || *prec == PB16;
+  *delta = h->opt.reliable_delta > 0.0 ? h->opt.reliable_delta : (half ? 0.3 : 0.1);
+  h->check = h->opt.check_every > 0 ? h->opt.check_every : (half ? 4 : 16);
   *restart = false;
   if (h->opt.solver == DWF_SOLVER_FP64) {
     *prec = P64;
@@ -1062,9 +1069,9 @@ int dwf_default_options(dwf_options* opt) {
   opt->bc_t = 1;
   opt->rel_tol = 1e-10;
   opt->maxiter = 100000;
-  opt->reliable_delta = 0.1;
+  opt->reliable_delta = 0.0;
   opt->solver = DWF_SOLVER_RELIABLE;
-  opt->check_every = 16;
+  opt->check_every = 0;
   opt->profile = 0;
   opt->graph = 1;
   opt->rhs_block = 0;
