@@ -203,6 +203,7 @@ struct dwf_ctx {
   int* nbr = nullptr;                            // [2][Vh][8] neighbour table
   int* dev_err = nullptr;                        // set by a kernel whose bounded wait gave up
   int use_tma = 0;                               // DWF_TMA: bulk-copy staged tuned kernels
+  bool fused_cg = true;                          // DWF_UNFUSED_CG unset: fused CG BLAS steps
   int check = 16;                                // effective iterations between polls
   bool gauge_loaded = false;
   std::vector<void*> allocs;
@@ -232,7 +233,7 @@ struct dwf_ctx {
 namespace {
 
 constexpr int kScal = 16;
-enum { S_ZZ0 = 0, S_ZZ1 = 1, S_WW = 2, S_RR = 3, S_RRHI = 4, S_BB = 5, S_T0 = 6, S_T1 = 7, S_T2 = 8 };
+enum { S_ZZ0 = 0, S_ZZ1 = 1, S_WW = 2, S_RR = 3, S_RRHI = 4, S_BB = 5, S_T0 = 6, S_T1 = 7, S_T2 = 8, S_A = 9 };
 
 int fail(dwf_ctx* h, int code, const std::string& msg) {
   if (h) h->err = msg;
@@ -447,17 +448,15 @@ int apply_dbb(dwf_ctx* h, const CoefView& cv, int prec, void* out, const void* i
   return DWF_OK;
 }
 
-// out = D_bb^+ in.  tmp_red: red field(s); tmp_blk: black field(s).
-int apply_dbb_dag(dwf_ctx* h, const CoefView& cv, int prec, void* out, const void* in, void* tmp_red,
-                  void* tmp_blk, int nrhs, const Reduce* norm, cudaStream_t s) {
+// hat = I^-T gamma5 in (the local first factor of D_bb^+).
+int apply_hat(dwf_ctx* h, const CoefView& cv, int prec, void* hat, const void* in, int nrhs,
+              cudaStream_t s) {
   const MatSet& ms = *cv.layout;
-  const int black = h->opt.rb_parity, red = 1 - black;
-  const size_t st = field_bytes(h->g, prec);
   LocalLaunch L{};
   L.prec = prec;
-  L.out = tmp_blk;
+  L.out = hat;
   L.in = in;
-  L.stride = st;
+  L.stride = field_bytes(h->g, prec);
   L.nrhs = nrhs;
   L.m = cv.ptr(prec, ms.mat_off(MatSet::IINVT));
   L.prog = hop2::PR_ITINV;
@@ -467,9 +466,18 @@ int apply_dbb_dag(dwf_ctx* h, const CoefView& cv, int prec, void* out, const voi
   L.cstride = cv.cstride;
   L.active = cv.active;
   KLAUNCH(h, launch_local(h->g, L, s));
+  return DWF_OK;
+}
+
+// out = D_bb^+ in given hat = I^-T gamma5 in.  tmp_red: red field(s).
+int apply_dbb_dag_hat(dwf_ctx* h, const CoefView& cv, int prec, void* out, const void* in,
+                      const void* hat, void* tmp_red, int nrhs, const Reduce* norm, cudaStream_t s) {
+  const MatSet& ms = *cv.layout;
+  const int black = h->opt.rb_parity, red = 1 - black;
+  const size_t st = field_bytes(h->g, prec);
   HopLaunch A = base_hop(h, prec, red, nrhs, st);
   A.out = tmp_red;
-  A.v = tmp_blk;
+  A.v = hat;
   A.post = cv.ptr(prec, ms.mat_off(MatSet::KT));
   A.post_prog = hop2::PR_KT;
   A.chain = cv.ptr(prec, ms.chain_off());
@@ -490,6 +498,14 @@ int apply_dbb_dag(dwf_ctx* h, const CoefView& cv, int prec, void* out, const voi
   set_coef(B, cv);
   KLAUNCH(h, launch_hop(h->g, B, s));
   return DWF_OK;
+}
+
+// out = D_bb^+ in.  tmp_red: red field(s); tmp_blk: black field(s).
+int apply_dbb_dag(dwf_ctx* h, const CoefView& cv, int prec, void* out, const void* in, void* tmp_red,
+                  void* tmp_blk, int nrhs, const Reduce* norm, cudaStream_t s) {
+  int rc;
+  if ((rc = apply_hat(h, cv, prec, tmp_blk, in, nrhs, s))) return rc;
+  return apply_dbb_dag_hat(h, cv, prec, out, in, tmp_blk, tmp_red, nrhs, norm, s);
 }
 
 // (out0, out1) = D_alpha(ms) (in0, in1), FP64 internal halves by parity.
@@ -625,7 +641,11 @@ int ensure_active(dwf_ctx* h, int nb) {
 // after every replacement).  One iteration:
 //   z = D^+ r (fused |z|^2), beta = |z|^2 / |z_prev|^2, p = z + beta p,
 //   w = D p (fused |w|^2), a = |z|^2 / |w|^2, x += a p, r -= a w (fused |r|^2);
-// the first beta is 0 (|z_prev|^2 starts at +inf).  The check iterations
+// the first beta is 0 (|z_prev|^2 starts at +inf).  With the tuned kernels
+// (Ls in {8, 12, 16}) the BLAS steps are fused differently, same arithmetic:
+// the residual update also writes r^ = I^-T gamma5 r (the first factor of the
+// next D^+ r) and stores a, and x += a p is deferred into the next p update
+// (flushed before every poll).  The check iterations
 // between two convergence polls are captured once as a CUDA graph.  Each right-
 // hand side has its own scalars, coefficients (cv.cstride) and convergence; the
 // device mask skips converged ones.  W.b_hi holds the nb FP64 sources, W.x_hi
@@ -691,8 +711,52 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
     }
   }
   if ((rc = push_active())) return rc;
+  const int Ls = h->g.Ls;
+  const bool fused = h->fused_cg && !g_disable_tuned && (Ls == 8 || Ls == 12 || Ls == 16);
+  if (fused && (rc = apply_hat(h, cv, prec, W.tb, W.r, nb, s))) return rc;
 
-  auto enqueue_iter = [&](int cur) -> int {
+  auto enqueue_fused = [&](int cur, bool first) -> int {
+    const int nxt = 1 - cur;
+    double* zz_new = h->scal + (nxt ? S_ZZ1 : S_ZZ0);
+    double* zz_old = h->scal + (cur ? S_ZZ1 : S_ZZ0);
+    int r;
+    if ((r = timer_mark(h, s, true, 1))) return r;
+    if ((r = apply_dbb_dag_hat(h, cv, prec, W.z, W.r, W.tb, W.tr, nb, &red_zz[nxt], s))) return r;
+    if ((r = timer_mark(h, s, false, 1))) return r;
+    if (first)
+      KLAUNCH(h, launch_p_update(h->g, prec, W.p, W.z, zz_new, zz_old, kScal, nb, fi, s, h->d_active));
+    else
+      KLAUNCH(h, launch_px_update(h->g, prec, xprec, W.xlo, W.p, W.z, h->scal + S_A, zz_new, zz_old,
+                                  kScal, nb, fx, fi, s, h->d_active));
+    if ((r = timer_mark(h, s, true, 0))) return r;
+    if ((r = apply_dbb(h, cv, prec, W.w, W.p, W.tr, nb, &red_ww, s))) return r;
+    if ((r = timer_mark(h, s, false, 0))) return r;
+    RUpdateLaunch U{};
+    U.prec = prec;
+    U.r = W.r;
+    U.rhat = W.tb;
+    U.w = W.w;
+    U.stride = fi;
+    U.nrhs = nb;
+    U.chain = cv.ptr(prec, cv.layout->chain_off());
+    U.cstride = cv.cstride;
+    U.num = zz_new;
+    U.den = h->scal + S_WW;
+    U.a_out = h->scal + S_A;
+    U.sstride = kScal;
+    U.red = &red_rr;
+    U.active = h->d_active;
+    KLAUNCH(h, launch_rupdate(h->g, U, s));
+    return DWF_OK;
+  };
+  auto flush_x = [&]() -> int {
+    if (fused)
+      KLAUNCH(h, launch_x_update(h->g, prec, xprec, W.xlo, W.p, h->scal + S_A, kScal, nb, fx, fi, s,
+                                 h->d_active));
+    return DWF_OK;
+  };
+  auto enqueue_iter = [&](int cur, bool first) -> int {
+    if (fused) return enqueue_fused(cur, first);
     const int nxt = 1 - cur;
     int r;
     if ((r = timer_mark(h, s, true, 1))) return r;
@@ -724,8 +788,8 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
     const long long l0 = h->launches;
     CUCHK(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
     int cur = 0;
-    for (int k = 0; k < check; k++) {
-      if ((rc = enqueue_iter(cur))) {
+    for (int k = 0; k <= check; k++) {
+      if ((rc = k < check ? enqueue_iter(cur, k == 0) : flush_x())) {
         cudaStreamEndCapture(s, &graph);
         cleanup();
         return rc;
@@ -752,9 +816,10 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
     } else {
       int cur = 0;
       for (int k = 0; k < check; k++) {
-        if ((rc = enqueue_iter(cur))) return rc;
+        if ((rc = enqueue_iter(cur, k == 0))) return rc;
         cur = 1 - cur;
       }
+      if ((rc = flush_x())) return rc;
     }
     it += check;
     for (int r = 0; r < nb; r++)
@@ -789,6 +854,10 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
       }
       KLAUNCH(h, launch_sub64_norm(h->g, W.r_hi, W.b_hi, W.t64, nb, f64, &red_hi, s, h->d_active));
       KLAUNCH(h, launch_convert(h->g, prec, W.r, P64, W.r_hi, nb, fi, f64, nullptr, s, h->d_active));
+      if (fused && (rc = apply_hat(h, cv, prec, W.tb, W.r, nb, s))) {
+        cleanup();
+        return rc;
+      }
       if ((rc = sync_read(h, nb, s))) {
         cleanup();
         return rc;
@@ -1119,6 +1188,7 @@ int dwf_create(dwf_handle* out, const int lattice[4], int Ls, double M5, double 
   // through shared memory with cp.async.bulk (measured slower than direct
   // loads on the 16^3x32 workload; kept as an alternative staging strategy).
   h->use_tma = std::getenv("DWF_TMA") != nullptr;
+  h->fused_cg = std::getenv("DWF_UNFUSED_CG") == nullptr;
   cudaGetDevice(&h->device);
   if (cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();

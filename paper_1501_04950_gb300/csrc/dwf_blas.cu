@@ -275,6 +275,38 @@ __global__ void __launch_bounds__(kBlasThreads) p_update_kernel(
   }
 }
 
+
+template <class SPX, class SP>
+__global__ void __launch_bounds__(kBlasThreads) px_update_kernel(
+    const Geom g, void* x, void* p, const void* z, const double* a_ptr, const double* num,
+    const double* den, int sstride, size_t stride_x, size_t stride, const int* active, int do_p) {
+  using T = typename SP::T;
+  using TX = typename SPX::T;
+  const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
+  const size_t off = rhs * stride, offx = rhs * stride_x;
+  const TX a = (TX)a_ptr[(size_t)rhs * sstride];
+  const T beta = do_p ? (T)(num[(size_t)rhs * sstride] / den[(size_t)rhs * sstride]) : (T)0;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
+    Spinor<T> pv;
+    Spinor<TX> xv;
+    SP::load(reinterpret_cast<const char*>(p) + off, n, g.N5, pv);
+    SPX::load(reinterpret_cast<const char*>(x) + offx, n, g.N5, xv);
+#pragma unroll
+    for (int k = 0; k < 12; k++)
+      xv.c[k] = cmake(fma(a, (TX)pv.c[k].re, xv.c[k].re), fma(a, (TX)pv.c[k].im, xv.c[k].im));
+    SPX::store(reinterpret_cast<char*>(x) + offx, n, g.N5, xv);
+    if (do_p) {
+      Spinor<T> zv;
+      SP::load(reinterpret_cast<const char*>(z) + off, n, g.N5, zv);
+#pragma unroll
+      for (int k = 0; k < 12; k++)
+        pv.c[k] = cmake(fma(beta, pv.c[k].re, zv.c[k].re), fma(beta, pv.c[k].im, zv.c[k].im));
+      SP::store(reinterpret_cast<char*>(p) + off, n, g.N5, pv);
+    }
+  }
+}
+
 template <class SPD, class SPS>
 __global__ void __launch_bounds__(kBlasThreads) convert_kernel(
     const Geom g, void* dst, const void* src, size_t sd, size_t ss, Reduce red, int do_norm,
@@ -487,6 +519,32 @@ cudaError_t launch_convert(const Geom& g, int prec_d, void* dst, int prec_s, con
     case PB16: return convert_from<Store16<true>>(g, dst, prec_s, src, nrhs, sd, ss, red, s, active);
   }
   return cudaErrorInvalidValue;
+}
+
+
+template <class SPX>
+cudaError_t px_from(const Geom& g, int prec, void* x, void* p, const void* z, const double* a_ptr,
+                    const double* num, const double* den, int sstride, int nrhs, size_t sx,
+                    size_t sp, cudaStream_t s, const int* active, int do_p) {
+  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  DWF_PREC_SWITCH(prec, SP, px_update_kernel<SPX, SP><<<grid, kBlasThreads, 0, s>>>(g, x, p, z, a_ptr, num, den, sstride, sx, sp, active, do_p));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_px_update(const Geom& g, int prec, int xprec, void* x, void* p, const void* z,
+                             const double* a_ptr, const double* num, const double* den,
+                             int sstride, int nrhs, size_t sx, size_t sp, cudaStream_t s,
+                             const int* active) {
+  if (xprec == P64) return px_from<Store64>(g, prec, x, p, z, a_ptr, num, den, sstride, nrhs, sx, sp, s, active, 1);
+  return px_from<Store32>(g, prec, x, p, z, a_ptr, num, den, sstride, nrhs, sx, sp, s, active, 1);
+}
+
+cudaError_t launch_x_update(const Geom& g, int prec, int xprec, void* x, const void* p,
+                            const double* a_ptr, int sstride, int nrhs, size_t sx, size_t sp,
+                            cudaStream_t s, const int* active) {
+  void* pp = const_cast<void*>(p);
+  if (xprec == P64) return px_from<Store64>(g, prec, x, pp, nullptr, a_ptr, a_ptr, a_ptr, sstride, nrhs, sx, sp, s, active, 0);
+  return px_from<Store32>(g, prec, x, pp, nullptr, a_ptr, a_ptr, a_ptr, sstride, nrhs, sx, sp, s, active, 0);
 }
 
 cudaError_t launch_accumulate64(const Geom& g, void* x64, int prec_s, void* src, int zero_src,

@@ -194,6 +194,18 @@ struct Store16 {
     for (int q = 0; q < 6; q++)
       o[q] = cmake(sc * to_f((uint16_t)(w[q] & 0xffffu)), sc * to_f((uint16_t)(w[q] >> 16)));
   }
+  // o <- what store() followed by load() gives back, computed in registers (a
+  // kernel must not re-read through __ldg what it wrote itself).
+  __device__ static void quantize(Spinor<float>& o) {
+    float mx = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; k++) mx = fmaxf(mx, fmaxf(fabsf(o.c[k].re), fabsf(o.c[k].im)));
+    const float sc = mx > 0.f ? mx : 1.f;
+    const float inv = 1.f / sc;
+#pragma unroll
+    for (int k = 0; k < 12; k++)
+      o.c[k] = cmake(sc * to_f(from_f(o.c[k].re * inv)), sc * to_f(from_f(o.c[k].im * inv)));
+  }
   __device__ static void store(void* base, int n, int N5, const Spinor<float>& o) {
     uint4* b = reinterpret_cast<uint4*>(base);
     float mx = 0.f;

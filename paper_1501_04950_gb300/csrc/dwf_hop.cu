@@ -423,6 +423,17 @@ cudaError_t launch_hop(const Geom& g, const HopLaunch& L, cudaStream_t st) {
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_rupdate(const Geom& g, const RUpdateLaunch& L, cudaStream_t st) {
+  if (g_disable_tuned) return cudaErrorNotSupported;
+  switch (L.prec) {
+    case P64: return launch_hop2_f64_rupdate(g, L, st);
+    case P32: return launch_hop2_f32_rupdate(g, L, st);
+    case P16: return launch_hop2_f16_rupdate(g, L, st);
+    case PB16: return launch_hop2_bf16_rupdate(g, L, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_local(const Geom& g, const LocalLaunch& L, cudaStream_t st) {
   if (!g_disable_tuned) {
     cudaError_t e = cudaErrorNotSupported;

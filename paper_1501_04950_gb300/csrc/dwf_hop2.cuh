@@ -927,6 +927,110 @@ cudaError_t dispatch_local(const Geom& g, const LocalLaunch& L, cudaStream_t st)
   return cudaErrorNotSupported;
 }
 
+
+// Fused CG residual update: r -= a w with a = num / den, |r|^2, and
+// r^ = I^-T gamma5 r (the input of the next D_bb^+ pass A), two slices per
+// thread; a is also stored to a_out (read by the next p/x update).
+template <class SP, int LS>
+__global__ void __launch_bounds__(128) rupdate_kernel(const Geom g, void* r, void* rhat,
+                                                      const void* w, size_t stride,
+                                                      const typename SP::T* chain, size_t cstride,
+                                                      const double* num, const double* den,
+                                                      double* a_out, int sstride, Reduce red,
+                                                      const int* rhs_on) {
+  using T = typename SP::T;
+  constexpr int SST = site_stride(LS);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  T* coef = reinterpret_cast<T*>(smem_raw);
+  T* sbuf = coef + chain_block(LS);
+  const int t = threadIdx.x, j = threadIdx.y;
+  const int nth = blockDim.x * blockDim.y, tid = j * blockDim.x + t;
+  const int h = blockIdx.x * blockDim.y + j;
+  const bool active = h < g.Vh;
+  const int rhs = blockIdx.z;
+  if (rhs_on && !rhs_on[rhs]) return;
+  const double ad = num[(size_t)rhs * sstride] / den[(size_t)rhs * sstride];
+  if (blockIdx.x == 0 && tid == 0) a_out[(size_t)rhs * sstride] = ad;
+  const T a = (T)ad;
+  for (int i = tid; i < chain_block(LS); i += nth) coef[i] = chain[(size_t)rhs * cstride + i];
+  const size_t off = rhs * stride;
+  const int n = h * LS + t, n1 = n + LS / 2;
+  Spinor<T> x0, x1;
+  double nrm = 0.0;
+#pragma unroll
+  for (int k = 0; k < 12; k++) {
+    x0.c[k] = cmake<T>(0, 0);
+    x1.c[k] = cmake<T>(0, 0);
+  }
+  if (active) {
+    Spinor<T> w0, w1;
+    SP::load(reinterpret_cast<const char*>(r) + off, n, g.N5, x0);
+    SP::load(reinterpret_cast<const char*>(r) + off, n1, g.N5, x1);
+    SP::load(reinterpret_cast<const char*>(w) + off, n, g.N5, w0);
+    SP::load(reinterpret_cast<const char*>(w) + off, n1, g.N5, w1);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      x0.c[k] = cmake(fma(-a, w0.c[k].re, x0.c[k].re), fma(-a, w0.c[k].im, x0.c[k].im));
+      x1.c[k] = cmake(fma(-a, w1.c[k].re, x1.c[k].re), fma(-a, w1.c[k].im, x1.c[k].im));
+    }
+    SP::store(reinterpret_cast<char*>(r) + off, n, g.N5, x0);
+    SP::store(reinterpret_cast<char*>(r) + off, n1, g.N5, x1);
+    if constexpr (SP::kScaled) {
+      // 16-bit storage rounds: r^ and |r|^2 follow the stored residual
+      SP::quantize(x0);
+      SP::quantize(x1);
+    }
+    nrm = sqr(x0) + sqr(x1);
+  }
+#pragma unroll
+  for (int k = 6; k < 12; k++) {
+    x0.c[k] = cmake(-x0.c[k].re, -x0.c[k].im);
+    x1.c[k] = cmake(-x1.c[k].re, -x1.c[k].im);
+  }
+  T* site = sbuf + j * SST;
+  const int s0 = 2 * t;
+  put(site + slot(s0), x0);
+  put(site + slot(s0) + 24, x1);
+  __syncthreads();
+  run_prog<T, LS, PR_ITINV>(site, coef, t);
+  __syncthreads();
+  get(site + slot(s0), x0);
+  get(site + slot(s0) + 24, x1);
+  if (active) {
+    SP::store(reinterpret_cast<char*>(rhat) + off, n, g.N5, x0);
+    SP::store(reinterpret_cast<char*>(rhat) + off, n1, g.N5, x1);
+  }
+  reduce_finish(nrm, red, rhs, gridDim.x, blockIdx.x);
+}
+
+template <class SP, int LS>
+cudaError_t run_rupdate(const Geom& g, const RUpdateLaunch& L, cudaStream_t st) {
+  using T = typename SP::T;
+  const int S = block_sites(LS);
+  const size_t smem = smem_bytes(LS, S, sizeof(T));
+  auto k = rupdate_kernel<SP, LS>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 block(LS / 2, S, 1);
+  dim3 grid((g.Vh + S - 1) / S, 1, L.nrhs);
+  k<<<grid, block, smem, st>>>(g, L.r, L.rhat, L.w, L.stride, reinterpret_cast<const T*>(L.chain),
+                               L.cstride, L.num, L.den, L.a_out, L.sstride, *L.red, L.active);
+  return cudaGetLastError();
+}
+
+template <class SP>
+cudaError_t dispatch_rupdate(const Geom& g, const RUpdateLaunch& L, cudaStream_t st) {
+  switch (g.Ls) {
+    case 8: return run_rupdate<SP, 8>(g, L, st);
+    case 12: return run_rupdate<SP, 12>(g, L, st);
+    case 16: return run_rupdate<SP, 16>(g, L, st);
+  }
+  return cudaErrorNotSupported;
+}
 }  // namespace hop2
 }  // namespace dwf
 
@@ -937,5 +1041,8 @@ cudaError_t dispatch_local(const Geom& g, const LocalLaunch& L, cudaStream_t st)
   }                                                                                      \
   cudaError_t NAME##_local(const Geom& g, const LocalLaunch& L, cudaStream_t st) {       \
     return hop2::dispatch_local<SP>(g, L, st);                                           \
+  }                                                                                      \
+  cudaError_t NAME##_rupdate(const Geom& g, const RUpdateLaunch& L, cudaStream_t st) {   \
+    return hop2::dispatch_rupdate<SP>(g, L, st);                                         \
   }                                                                                      \
   }

@@ -120,6 +120,39 @@ cudaError_t launch_hop2_f64_local(const Geom& g, const LocalLaunch& a, cudaStrea
 cudaError_t launch_hop2_f32_local(const Geom& g, const LocalLaunch& a, cudaStream_t s);
 cudaError_t launch_hop2_f16_local(const Geom& g, const LocalLaunch& a, cudaStream_t s);
 cudaError_t launch_hop2_bf16_local(const Geom& g, const LocalLaunch& a, cudaStream_t s);
+// Fused CG residual update of the tuned path (Ls in {8, 12, 16}):
+// r -= a w (a = num/den, stored to a_out), |r|^2 -> red, rhat = I^-T gamma5 r.
+struct RUpdateLaunch {
+  int prec;
+  void* r;
+  void* rhat;
+  const void* w;
+  size_t stride;
+  int nrhs;
+  const void* chain;
+  size_t cstride;
+  const double* num;
+  const double* den;
+  double* a_out;
+  int sstride;
+  const Reduce* red;
+  const int* active;
+};
+cudaError_t launch_rupdate(const Geom& g, const RUpdateLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_f64_rupdate(const Geom& g, const RUpdateLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_f32_rupdate(const Geom& g, const RUpdateLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_f16_rupdate(const Geom& g, const RUpdateLaunch& a, cudaStream_t s);
+cudaError_t launch_hop2_bf16_rupdate(const Geom& g, const RUpdateLaunch& a, cudaStream_t s);
+// x += a_prev p; p = z + beta p (a_prev = *a_ptr, beta = num / den); x in xprec.
+cudaError_t launch_px_update(const Geom& g, int prec, int xprec, void* x, void* p, const void* z,
+                             const double* a_ptr, const double* num, const double* den,
+                             int sstride, int nrhs, size_t stride_x, size_t stride,
+                             cudaStream_t s, const int* active);
+// x += a p, a = *a_ptr (flush of the deferred solution update).
+cudaError_t launch_x_update(const Geom& g, int prec, int xprec, void* x, const void* p,
+                            const double* a_ptr, int sstride, int nrhs, size_t stride_x,
+                            size_t stride, cudaStream_t s, const int* active);
+
 // Set to 1 to force the generic kernels (tests compare both paths).
 extern int g_disable_tuned;
 

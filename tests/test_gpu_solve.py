@@ -102,3 +102,24 @@ def test_batched_solve(rhs_block, graph):
             assert st[kk]["true_resid"] <= 1e-10
             assert np.abs(p[kk] - ref["z1"]).max() / np.abs(ref["z1"]).max() < 1e-7
     assert all(x["iterations"] > 0 and x["seconds"] > 0 for x in st)
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_fused_and_unfused_cg_agree(prec, monkeypatch):
+    """Tuned-kernel CG (fused residual update + deferred x update) and the
+    unfused BLAS steps (DWF_UNFUSED_CG) both reach 1e-10 and the same z_1."""
+    L = (4, 4, 4, 8)
+    src = gaussian_source4d(L, seed=4, even_only=True)
+    sysm = make_case(L, 8, "mobius", alpha=1.5, m=0.02, eps=0.3)
+    out = {}
+    for fused in (True, False):
+        if fused:
+            monkeypatch.delenv("DWF_UNFUSED_CG", raising=False)
+        else:
+            monkeypatch.setenv("DWF_UNFUSED_CG", "1")
+        prop, _, st = _solve(sysm, src, precision_inner=prec, maxiter=20000)
+        print("prec %d fused %d: iters %d restarts %d resid %.2e"
+              % (prec, fused, st[0]["iterations"], st[0]["restarts"], st[0]["true_resid"]))
+        assert st[0]["true_resid"] <= 1e-10
+        out[fused] = prop
+    assert np.abs(out[True] - out[False]).max() / np.abs(out[True]).max() < 1e-8
