@@ -261,6 +261,43 @@ def run_batched(args):
     return out
 
 
+def run_zolotarev(args):
+    """Zolotarev alpha-Mobius solve, 24^3x48, Ls = 12 (b_i + c_i = 1/omega_i from the
+    minimax sign approximation on [0.05, 6], concave order), m = 0.005, alpha = 1.25,
+    Gaussian b_1: time to FP64 true residual 1e-10 per inner precision and solver."""
+    import torch
+    from paper_1501_04950_gb300 import dwf
+    from synthetic import gauge_field, gaussian_source4d, zolotarev_mobius
+    dev = torch.device("cuda", 0)
+    L, Ls, m, alpha = (24, 24, 24, 48), 12, 0.005, 1.25
+    b, c, _, _ = zolotarev_mobius(Ls, 0.05, 6.0)
+    U = torch.from_numpy(gauge_field(L, EPS, seed=0)).to(dev)
+    src = torch.from_numpy(gaussian_source4d(L, seed=1)).to(dev)
+    prop = torch.empty_like(src)
+    row = {"workload": "24^3x48 Ls=12 Zolotarev [0.05,6] concave, M5=-1.8 m=0.005 alpha=1.25 "
+                       "eps=0.5, Gaussian b_1; CGNE to FP64 true residual 1e-10"}
+    variants = [("fp32_reliable", dict(precision_inner=dwf.FP32)),
+                ("fp16_reliable", dict(precision_inner=dwf.FP16)),
+                ("fp16_defect", dict(precision_inner=dwf.FP16, solver=dwf.SOLVER_DEFECT)),
+                ("bf16_defect", dict(precision_inner=dwf.BF16, solver=dwf.SOLVER_DEFECT)),
+                ("fp64", dict(solver=dwf.SOLVER_FP64))]
+    for name, opts in variants:
+        op = dwf.DWF(L, Ls, M5, m, alpha, b, c, maxiter=100000, **opts)
+        op.load_gauge(U)
+        op.cgne_solve(src, prop, allow_not_converged=True)  # warm-up (autotune, graph)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = op.cgne_solve(src, prop, allow_not_converged=True)[0]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        row[name] = {"solve_ms": dt * 1e3, "iterations": st["iterations"],
+                     "restarts": st["restarts"], "true_resid": st["true_resid"],
+                     "true_resid_5d": st["true_resid_5d"]}
+        op.close()
+    print(json.dumps(row), flush=True)
+    return row
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -279,6 +316,8 @@ def main():
     ap.add_argument("--batched", default=None,
                     help="batched mode: comma-separated lattices such as 8x8x8x8,16x16x16x32; "
                          "12 spin-colour point sources x alpha in {1, 1.5} per lattice")
+    ap.add_argument("--zolotarev", action="store_true",
+                    help="Zolotarev 24^3x48, Ls=12, m=0.005 solve per inner precision")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -294,6 +333,9 @@ def main():
         return
     if args.batched:
         run_batched(args)
+        return
+    if args.zolotarev:
+        run_zolotarev(args)
         return
 
     import torch

@@ -67,7 +67,11 @@ enum { DWF_FP64 = 0, DWF_FP32 = 1, DWF_FP16 = 2, DWF_BF16 = 3 };
 
 /* Solver variants of dwf_cgne_solve. */
 enum {
-  DWF_SOLVER_RELIABLE = 0, /* inner precision CG with FP64 reliable updates (default) */
+  DWF_SOLVER_RELIABLE = 0, /* inner precision CG with FP64 reliable updates (default);
+                              with BF16 inner fields the recurrence restarts at every
+                              update (as DWF_SOLVER_DEFECT), and with any precision it
+                              restarts after an update that gained < 10%; five such
+                              updates in a row end the solve (DWF_ERR_NOT_CONVERGED) */
   DWF_SOLVER_DEFECT = 1,   /* FP64 defect correction around restarted inner CG      */
   DWF_SOLVER_FP64 = 2      /* plain FP64 CG on the normal equations                 */
 };
@@ -79,10 +83,10 @@ typedef struct {
   double rel_tol;        /* target |r'_b - D_bb x| / |r'_b| (default 1e-10)          */
   int maxiter;           /* total inner iterations per right-hand side (default 100000) */
   double reliable_delta; /* reliable update when |r| < delta * max|r|; <= 0 (default):
-                            0.1 for FP32 inner fields, 0.3 for FP16/BF16              */
+                            0.5 for FP16 inner fields, 0.1 otherwise                  */
   int solver;            /* DWF_SOLVER_* (default DWF_SOLVER_RELIABLE)               */
-  int check_every;       /* iterations between convergence polls; <= 0 (default): 16,
-                            4 for FP16/BF16 inner fields                               */
+  int check_every;       /* iterations between convergence polls; <= 0 (default): 4 for
+                            FP16 inner fields, 16 otherwise                            */
   int profile;           /* 1: time the inner applies with CUDA events (stats.apply_ms) */
   int graph;             /* 1 (default): replay the CG iterations between polls as a CUDA graph */
   int rhs_block;         /* right-hand sides solved together: 0 (default) = autotuned        */

@@ -13,20 +13,28 @@ site: row i is b_i (D_w - (4 + M5)) v_plus_i + c_i (D_w - (4 + M5)) v_minus_i
 with v_plus_i / v_minus_i the block sums of Eq. mobius1 at the neighbour
 sites, and (D_w - (4 + M5)) v(y) = -1/2 sum_mu [(1 - gamma_mu) U_mu(y)
 v(y + mu) + (1 + gamma_mu) U_mu(y - mu)^+ v(y - mu)] (Eq. wilson).
+
+PointwiseDalpha evaluates the full 5D equation of Sec. 2 at one 4D site,
+(D_alpha psi)(x) = I psi(x) + ((D_alpha - I) psi)(x), and the propagator
+right-hand side rhs = D_1(1) P b of Eq. tosolve with b = (b_1, 0, ..., 0),
+(P b)_s = P_- b_s + P_+ b_{s+1} (App. A, Eq. eqP), so that a solution psi of
+any size can be checked at sampled sites.
 """
 from __future__ import annotations
 
 import numpy as np
 
 from .dwf import blocks
-from .lattice import GAMMA, ID4
+from .lattice import GAMMA, ID4, P_MINUS, P_PLUS
+from .schur import DWFSystem
 
 
-class PointwiseDbb:
+class _SiteOps:
+    """Single-site pieces of Eq. mobius1 / Eq. wilson shared by the evaluators."""
+
     def __init__(self, sys):
         self.sys = sys
         self.Lx, self.Ly, self.Lz, self.Lt = sys.lattice
-        self.iinv = sys.local_inverse().reshape(sys.Ls, 4, sys.Ls, 4)
         self.blk = blocks(sys.Ls, sys.alpha, sys.m)
 
     def _lex(self, c):
@@ -83,6 +91,11 @@ class PointwiseDbb:
         c_ = sys.c.reshape(Ls, 1, 1)
         return b * wp + c_ * wm
 
+class PointwiseDbb(_SiteOps):
+    def __init__(self, sys):
+        super().__init__(sys)
+        self.iinv = sys.local_inverse().reshape(sys.Ls, 4, sys.Ls, 4)
+
     def _iinv(self, f):
         return np.einsum("aibj,bjc->aic", self.iinv, f)
 
@@ -107,3 +120,35 @@ class PointwiseDbb:
             return cache[c]
 
         return psi_at(site) - self._iinv(self._hop_part(site, u_at))
+
+
+class PointwiseDalpha(_SiteOps):
+    """D_alpha(m) of Sec. 2 (Eq. mobius1) and rhs = D_1(1) P b at single 4D sites."""
+
+    def __init__(self, sys):
+        super().__init__(sys)
+        self.imat = sys.local_matrix().reshape(sys.Ls, 4, sys.Ls, 4)
+        one = DWFSystem(sys.lattice, sys.Ls, sys.M5, 1.0, 1.0, sys.b, sys.c, sys.U,
+                        bc_t=sys.bc_t, black_parity=sys.black_parity)
+        self._d11 = _SiteOps(one)
+        self._d11_imat = one.local_matrix().reshape(sys.Ls, 4, sys.Ls, 4)
+
+    def apply_at(self, field_at, site):
+        """(D_alpha psi)(site) [Ls][4][3]; field_at(c) -> psi at 4D site c, [Ls][4][3]."""
+        return (np.einsum("aibj,bjc->aic", self.imat, field_at(site))
+                + self._hop_part(site, field_at))
+
+    def rhs_at(self, src4d, site):
+        """(D_1(1) P b)(site) for b = (b_1, 0, ..., 0), b_1 = src4d [t][z][y][x][4][3]."""
+        Ls = self.sys.Ls
+
+        def pb_at(c):
+            x, y, z, t = c
+            b1 = src4d[t, z, y, x]
+            v = np.zeros((Ls, 4, 3), dtype=np.complex128)
+            v[0] = P_MINUS @ b1
+            v[Ls - 1] = P_PLUS @ b1
+            return v
+
+        return (np.einsum("aibj,bjc->aic", self._d11_imat, pb_at(site))
+                + self._d11._hop_part(site, pb_at))

@@ -673,11 +673,12 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
   };
   CoefView cv = cv_in;
   cv.active = h->d_active;
-  auto push_active = [&]() -> int {
-    for (int r = 0; r < nb; r++) h->pinned_i[r] = act[r];
+  auto push_mask = [&](const std::vector<int>& mask) -> int {
+    for (int r = 0; r < nb; r++) h->pinned_i[r] = mask[r];
     CUCHK(h, cudaMemcpyAsync(h->d_active, h->pinned_i, sizeof(int) * nb, cudaMemcpyHostToDevice, s));
     return DWF_OK;
   };
+  auto push_active = [&]() -> int { return push_mask(act); };
   // |z_prev|^2 = +inf for the listed right-hand sides (first beta = 0)
   double* inf_src = reinterpret_cast<double*>(h->pinned_i + ((nb + 1) & ~1));
   auto reset_beta = [&](const std::vector<int>& which) -> int {
@@ -829,6 +830,7 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
       return rc;
     }
     bool update = false, changed = false;
+    std::vector<int> upd(nb, 0);
     for (int r = 0; r < nb; r++) {
       if (!act[r]) continue;
       const double rr = h->pinned[(size_t)r * kScal + S_RR], ww = h->pinned[(size_t)r * kScal + S_WW];
@@ -839,14 +841,22 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
         continue;
       }
       const double rn = std::sqrt(rr);
-      if (rn < delta * rmax[r] || rn <= tol * bnorm[r] || it >= maxiter) update = true;
+      if (rn < delta * rmax[r] || rn <= tol * bnorm[r] || it >= maxiter) {
+        upd[r] = 1;
+        update = true;
+      }
     }
-    if (changed && (rc = push_active())) {
+    if (changed && !update && (rc = push_active())) {
       cleanup();
       return rc;
     }
     if (update) {
-      // reliable update of every active right-hand side: x_hi += x_lo, r = b - D x_hi (FP64)
+      // reliable update of the right-hand sides that reached their threshold (the
+      // device mask selects them): x_hi += x_lo, r = b - D x_hi (FP64)
+      if ((rc = push_mask(upd))) {
+        cleanup();
+        return rc;
+      }
       KLAUNCH(h, launch_accumulate64(h->g, W.x_hi, xprec, W.xlo, 1, nb, f64, fx, s, h->d_active));
       if ((rc = apply_dbb(h, cv, P64, W.t64, W.x_hi, W.t64r, nb, nullptr, s))) {
         cleanup();
@@ -864,7 +874,7 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
       }
       std::vector<int> restarted(nb, 0);
       for (int r = 0; r < nb; r++) {
-        if (!act[r]) continue;
+        if (!upd[r]) continue;
         const double rrh = h->pinned[(size_t)r * kScal + S_RRHI];
         true_res[r] = std::sqrt(rrh) / bnorm[r];
         rmax[r] = std::sqrt(rrh);
@@ -875,19 +885,24 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
           t_done[r] = now_s();
           continue;
         }
-        // stagnation: three residual replacements in a row without a 10% gain
+        // A replacement without a 10% gain of the true residual means the
+        // low-precision recurrence has lost conjugacy: restart it (beta = 0).
+        // Five such replacements in a row: stagnation, stop.
         if (true_res[r] < 0.9 * best[r]) {
           best[r] = true_res[r];
           stalled[r] = 0;
-        } else if (++stalled[r] >= 3) {
+        } else if (++stalled[r] >= 5) {
           act[r] = 0;
           code[r] = DWF_ERR_NOT_CONVERGED;
           t_done[r] = now_s();
           continue;
+        } else {
+          restarted[r] = 1;
         }
         if (restart) restarted[r] = 1;
       }
-      if (restart && (rc = reset_beta(restarted))) {
+      if (std::any_of(restarted.begin(), restarted.end(), [](int v) { return v != 0; }) &&
+          (rc = reset_beta(restarted))) {
         cleanup();
         return rc;
       }
@@ -1020,18 +1035,23 @@ int cgnormal_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxit
 }
 
 // Effective solver settings.  reliable_delta <= 0 and check_every <= 0 select
-// precision-dependent defaults: 16-bit inner fields drift from the true residual
-// within a few iterations, so they replace it more often (delta 0.3, poll every
-// 4 iterations) than FP32 (0.1, every 16).
+// precision-dependent defaults, measured on 8^4 x 16 point-source solves:
+//   FP32: delta 0.1, poll every 16 iterations;
+//   FP16: delta 0.5, every 4 (its 11-bit significand drifts from the true
+//         residual within a few iterations);
+//   BF16: delta 0.1, every 16, and the reliable-update solver restarts the
+//         recurrence at every replacement (defect correction): with an 8-bit
+//         significand the unrestarted recurrence loses conjugacy.
 int solver_params(dwf_ctx* h, int* prec, double* delta, bool* restart) {
   *prec = h->opt.precision_inner;
-  const bool half = *prec == P16 || *prec == PB16;
-  *delta = h->opt.reliable_delta > 0.0 ? h->opt.reliable_delta : (half ? 0.3 : 0.1);
-  h->check = h->opt.check_every > 0 ? h->opt.check_every : (half ? 4 : 16);
-  *restart = false;
+  const bool f16 = *prec == P16, b16 = *prec == PB16;
+  *delta = h->opt.reliable_delta > 0.0 ? h->opt.reliable_delta : (f16 ? 0.5 : 0.1);
+  h->check = h->opt.check_every > 0 ? h->opt.check_every : (f16 ? 4 : 16);
+  *restart = b16;
   if (h->opt.solver == DWF_SOLVER_FP64) {
     *prec = P64;
     *delta = 0.0;
+    *restart = false;
   } else if (h->opt.solver == DWF_SOLVER_DEFECT) {
     *restart = true;
   }

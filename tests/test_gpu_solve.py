@@ -123,3 +123,27 @@ def test_fused_and_unfused_cg_agree(prec, monkeypatch):
         assert st[0]["true_resid"] <= 1e-10
         out[fused] = prop
     assert np.abs(out[True] - out[False]).max() / np.abs(out[True]).max() < 1e-8
+
+
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_batched_mixed_alpha_16bit(prec):
+    """Point sources at alpha 1 and 1.5 in one block: each right-hand side takes
+    its own reliable-update decisions, so all converge; z_1 does not depend on
+    alpha (Eq. tosolve1)."""
+    from paper_1501_04950_gb300 import dwf
+    from synthetic import point_source4d
+    L = (8, 8, 8, 8)
+    Ls = 8
+    sysm = make_case(L, Ls, "mobius", alpha=1.0, m=0.01)
+    srcs = [point_source4d(L, sp, c) for sp, c in ((0, 0), (1, 1), (2, 2), (3, 0), (0, 2), (2, 1))]
+    src = torch.from_numpy(np.stack(srcs + srcs)).cuda()
+    op = dwf.DWF(L, Ls, sysm.M5, sysm.m, 1.0, sysm.b, sysm.c, precision_inner=prec,
+                 rhs_block=12, maxiter=20000)
+    op.load_gauge(torch.from_numpy(sysm.U).cuda())
+    prop = torch.empty_like(src)
+    st = op.cgne_solve(src, prop, nrhs=12, alphas=[1.0] * 6 + [1.5] * 6)
+    p = prop.cpu().numpy()
+    print("prec %d iterations %s" % (prec, [x["iterations"] for x in st]))
+    assert all(x["true_resid"] <= 1e-10 for x in st)
+    for k in range(6):
+        assert np.abs(p[k] - p[k + 6]).max() / np.abs(p[k]).max() < 1e-7
