@@ -83,10 +83,10 @@ typedef struct {
   double rel_tol;        /* target |r'_b - D_bb x| / |r'_b| (default 1e-10)          */
   int maxiter;           /* total inner iterations per right-hand side (default 100000) */
   double reliable_delta; /* reliable update when |r| < delta * max|r|; <= 0 (default):
-                            0.5 for FP16 inner fields, 0.1 otherwise                  */
+                            0.5 for FP16/BF16 inner fields, 0.1 otherwise             */
   int solver;            /* DWF_SOLVER_* (default DWF_SOLVER_RELIABLE)               */
   int check_every;       /* iterations between convergence polls; <= 0 (default): 4 for
-                            FP16 inner fields, 16 otherwise                            */
+                            FP16/BF16 inner fields, 16 otherwise                       */
   int profile;           /* 1: time the inner applies with CUDA events (stats.apply_ms) */
   int graph;             /* 1 (default): replay the CG iterations between polls as a CUDA graph */
   int rhs_block;         /* right-hand sides solved together: 0 (default) = autotuned        */

@@ -1039,14 +1039,16 @@ int cgnormal_solve(dwf_ctx* h, const MatSet& ms, int prec, double tol, int maxit
 //   FP32: delta 0.1, poll every 16 iterations;
 //   FP16: delta 0.5, every 4 (its 11-bit significand drifts from the true
 //         residual within a few iterations);
-//   BF16: delta 0.1, every 16, and the reliable-update solver restarts the
+//   BF16: delta 0.5, every 4, and the reliable-update solver restarts the
 //         recurrence at every replacement (defect correction): with an 8-bit
-//         significand the unrestarted recurrence loses conjugacy.
+//         significand the unrestarted recurrence loses conjugacy, and at
+//         delta 0.1 the inner solve of a Zolotarev m = 0.005 system never
+//         reached its threshold.
 int solver_params(dwf_ctx* h, int* prec, double* delta, bool* restart) {
   *prec = h->opt.precision_inner;
-  const bool f16 = *prec == P16, b16 = *prec == PB16;
-  *delta = h->opt.reliable_delta > 0.0 ? h->opt.reliable_delta : (f16 ? 0.5 : 0.1);
-  h->check = h->opt.check_every > 0 ? h->opt.check_every : (f16 ? 4 : 16);
+  const bool b16 = *prec == PB16, half = *prec == P16 || b16;
+  *delta = h->opt.reliable_delta > 0.0 ? h->opt.reliable_delta : (half ? 0.5 : 0.1);
+  h->check = h->opt.check_every > 0 ? h->opt.check_every : (half ? 4 : 16);
   *restart = b16;
   if (h->opt.solver == DWF_SOLVER_FP64) {
     *prec = P64;

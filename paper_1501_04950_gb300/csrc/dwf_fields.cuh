@@ -385,6 +385,40 @@ __device__ __forceinline__ void reconstruct_add(Spinor<T>& acc, const cplx<T> c0
   }
 }
 
+// acc += f (chi, -sg A^+ chi) with a runtime factor f (the +-1 of a hop across
+// an antiperiodic boundary): the factor rides on the accumulating FMAs.
+template <typename T>
+__device__ __forceinline__ void fmac(cplx<T>& acc, T f, const cplx<T>& c) {
+  acc = cmake(fma(f, c.re, acc.re), fma(f, c.im, acc.im));
+}
+template <typename T>
+__device__ __forceinline__ void fmac_i(cplx<T>& acc, T f, const cplx<T>& c) {  // acc += f i c
+  acc = cmake(fma(-f, c.im, acc.re), fma(f, c.re, acc.im));
+}
+template <typename T, int MU, int SG>
+__device__ __forceinline__ void reconstruct_add(Spinor<T>& acc, const cplx<T> c0[3], const cplx<T> c1[3],
+                                                T f) {
+  const T m = SG > 0 ? -f : f;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    fmac(acc.c[a], f, c0[a]);
+    fmac(acc.c[3 + a], f, c1[a]);
+    if (MU == 0) {         // A^+ chi = (i c1, i c0)
+      fmac_i(acc.c[6 + a], m, c1[a]);
+      fmac_i(acc.c[9 + a], m, c0[a]);
+    } else if (MU == 1) {  // A^+ chi = (c1, -c0)
+      fmac(acc.c[6 + a], m, c1[a]);
+      fmac(acc.c[9 + a], -m, c0[a]);
+    } else if (MU == 2) {  // A^+ chi = (i c0, -i c1)
+      fmac_i(acc.c[6 + a], m, c0[a]);
+      fmac_i(acc.c[9 + a], -m, c1[a]);
+    } else {               // A^+ chi = (c0, c1)
+      fmac(acc.c[6 + a], m, c0[a]);
+      fmac(acc.c[9 + a], m, c1[a]);
+    }
+  }
+}
+
 // chi = U h (DAG = false) or U^+ h (DAG = true), for both half-spinor rows.
 template <typename T, bool DAG>
 __device__ __forceinline__ void su3_mul(const Link<T>& U, const cplx<T> h0[3], const cplx<T> h1[3],
