@@ -76,6 +76,19 @@ enum {
   DWF_SOLVER_FP64 = 2      /* plain FP64 CG on the normal equations                 */
 };
 
+/* Red-black operator the CG runs on (Sec. 3).  All three have the same solution
+ * psi_b; they differ in conditioning, hence in iteration count.
+ *   DWF_SCHUR_PRECOND:   D_bb = 1 - I^-1 D_br I^-1 D_rb (Eq. redblack, default);
+ *   DWF_SCHUR_PLAIN:     I_bb - D_br I^-1 D_rb = I D_bb (Eq. redblack1), on
+ *                        I r'_b;
+ *   DWF_SCHUR_ROWSCALED: S I D_bb on S I r'_b, S = diag over the 5th dimension of
+ *                        1/(b_s + c_s) where b_s + c_s > 1, else 1 (the left row
+ *                        scaling discussed with Eq. redblack1).
+ * rel_tol and dwf_stats.true_resid then refer to that operator's own residual
+ * |L (r'_b - D_bb x)| / |L r'_b| (L = 1, I or S I); the forms other than
+ * DWF_SCHUR_PRECOND use the unfused CG steps and dense site-local kernels. */
+enum { DWF_SCHUR_PRECOND = 0, DWF_SCHUR_PLAIN = 1, DWF_SCHUR_ROWSCALED = 2 };
+
 typedef struct {
   int precision_inner;   /* DWF_FP32 (default), DWF_FP16, DWF_BF16 or DWF_FP64     */
   int rb_parity;         /* 0: black = even sites (default), 1: black = odd sites  */
@@ -90,6 +103,7 @@ typedef struct {
   int profile;           /* 1: time the inner applies with CUDA events (stats.apply_ms) */
   int graph;             /* 1 (default): replay the CG iterations between polls as a CUDA graph */
   int rhs_block;         /* right-hand sides solved together: 0 (default) = autotuned        */
+  int schur_form;        /* DWF_SCHUR_* operator of dwf_cgne_solve (default PRECOND)       */
 } dwf_options;
 
 typedef struct {

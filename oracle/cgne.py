@@ -77,8 +77,12 @@ def propagator_rhs(sys: DWFSystem, src4d):
     return dalpha(p_apply(b5), sys.U, sys.M5, sys.b, sys.c, 1.0, 1.0, sys.bc_t)
 
 
-def solve_propagator(sys: DWFSystem, src4d, tol=1e-10, maxiter=100000):
+def solve_propagator(sys: DWFSystem, src4d, tol=1e-10, maxiter=100000, form=0):
     """Red-black CGNR solve of D_alpha(m) P z = D_1(1) P b.
+
+    form selects the red-black operator of Sec. 3 (0: Eq. redblack, 1: Eq.
+    redblack1, 2: Eq. redblack1 with scaled rows); tol applies to that
+    operator's own residual.
 
     Returns dict with z1 (4D propagator), psi (full 5D solution of
     D_alpha psi = rhs), z (= P^-1 psi), iterations, the Schur-system true
@@ -86,7 +90,8 @@ def solve_propagator(sys: DWFSystem, src4d, tol=1e-10, maxiter=100000):
     """
     rhs = propagator_rhs(sys, src4d)
     rb = sys.schur_rhs(rhs)
-    xb, it, res = cgnr(sys.dbb, sys.dbb_dag, rb, tol=tol, maxiter=maxiter)
+    op, op_dag, left = sys.schur_operator(form)
+    xb, it, res = cgnr(op, op_dag, left(rb), tol=tol, maxiter=maxiter)
     psi = sys.reconstruct(xb, rhs)
     r5 = rhs - dalpha(psi, sys.U, sys.M5, sys.b, sys.c, sys.alpha, sys.m, sys.bc_t)
     res5 = np.sqrt(norm2(r5) / norm2(rhs))

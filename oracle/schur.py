@@ -23,6 +23,15 @@ with the parity blocks of (D_alpha - I)^dagger built from the literal
 adjoint of Eq. mobius1.
 
 The black parity is the even sites unless black_parity = 1 is given.
+
+Sec. 3 contrasts Eq. redblack with the older form of Eq. redblack1,
+    D_bb^(1) = I_bb - D_br I_rr^-1 D_rb ,
+and with that form's rows scaled from the left: every row s whose
+coefficient b_s + c_s (= 1/omega_s for Zolotarev coefficients) exceeds one is
+multiplied by 1 / (b_s + c_s).  schur_form 1 and 2 give these operators
+(2: S D_bb^(1) with S the diagonal of the row factors); the right-hand side
+of form k is the same left factor applied to I r'_b, so the solution psi_b
+is the same for all three forms.
 """
 from __future__ import annotations
 
@@ -139,6 +148,37 @@ class DWFSystem:
     def dbb_dag(self, hb):
         """D_bb^dagger phi_b = phi_b - D_rb^+ (I^-1)^+ D_br^+ (I^-1)^+ phi_b."""
         return hb - self.d_rb_dag(self.iinv_dag(self.d_br_dag(self.iinv_dag(hb))))
+
+    # --- Eq. redblack1 and its row-scaled form (Sec. 3) --------------------
+    def row_scale(self):
+        """S_s = 1 / (b_s + c_s) where b_s + c_s > 1, else 1."""
+        a = self.b + self.c
+        return np.where(a > 1.0, 1.0 / a, 1.0)
+
+    def _scale_rows(self, h):
+        return self.row_scale().reshape(self.Ls, 1, 1, 1) * h
+
+    def dbb_plain(self, hb):
+        """I_bb psi_b - D_br I^-1 D_rb psi_b (Eq. redblack1)."""
+        return self.apply_local_matrix(self.local_matrix(), hb) - self.d_br(self.iinv(self.d_rb(hb)))
+
+    def dbb_plain_dag(self, hb):
+        """(Eq. redblack1)^dagger = I^+ - D_rb^+ (I^-1)^+ D_br^+."""
+        return (self.apply_local_matrix(np.conj(self.local_matrix().T), hb)
+                - self.d_rb_dag(self.iinv_dag(self.d_br_dag(hb))))
+
+    def schur_operator(self, form):
+        """(apply, apply_dagger, left factor of the right-hand side) of form 0, 1 or 2."""
+        if form == 0:
+            return self.dbb, self.dbb_dag, lambda r: r
+        if form == 1:
+            return (self.dbb_plain, self.dbb_plain_dag,
+                    lambda r: self.apply_local_matrix(self.local_matrix(), r))
+        if form == 2:
+            return (lambda h: self._scale_rows(self.dbb_plain(h)),
+                    lambda h: self.dbb_plain_dag(self._scale_rows(h)),
+                    lambda r: self._scale_rows(self.apply_local_matrix(self.local_matrix(), r)))
+        raise ValueError("schur form must be 0, 1 or 2")
 
     def schur_rhs(self, rhs_full):
         """r'_b = I^-1 (rhs_b - D_br I^-1 rhs_r) from a full 5D right-hand side."""

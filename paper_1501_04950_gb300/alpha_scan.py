@@ -48,8 +48,11 @@ def row_coefficients(row):
 
 
 def scan(row, lattice=(16, 16, 16, 32), alphas=None, fields=1, eps=0.5, M5=-1.8, tol=1e-8,
-         precision=None, sources=12, device="cuda"):
-    """Run the scan for one row; returns a dict of per-alpha ratio statistics."""
+         precision=None, sources=12, device="cuda", form=0):
+    """Run the scan for one row; returns a dict of per-alpha ratio statistics.
+
+    form selects the red-black operator of Sec. 3 (dwf.SCHUR_*: 0 Eq. redblack,
+    1 Eq. redblack1, 2 Eq. redblack1 with scaled rows)."""
     import torch
     from synthetic import gauge_field, point_source4d
     from . import dwf
@@ -71,7 +74,7 @@ def scan(row, lattice=(16, 16, 16, 32), alphas=None, fields=1, eps=0.5, M5=-1.8,
         al = [a for a in alphas for _ in pts]
         # poll every 2 iterations: the counts are exact to 2 instead of 16
         op = dwf.DWF(lattice, Ls, M5, mass, 1.0, b, c, rel_tol=tol, precision_inner=precision,
-                     check_every=2)
+                     check_every=2, schur_form=form)
         op.load_gauge(U)
         prop = torch.empty_like(src)
         st = op.cgne_solve(src, prop, nrhs=len(al), alphas=al)
@@ -86,7 +89,7 @@ def scan(row, lattice=(16, 16, 16, 32), alphas=None, fields=1, eps=0.5, M5=-1.8,
     return {
         "row": {"mass": mass, "Ls": Ls, "b": "zolotarev" if row[2] is None else row[2],
                 "c": "zolotarev" if row[3] is None else row[3]},
-        "lattice": list(lattice), "fields": fields, "sources": len(pts), "tol": tol,
+        "form": form, "lattice": list(lattice), "fields": fields, "sources": len(pts), "tol": tol,
         "alphas": alphas, "ratio_mean": mean.tolist(), "ratio_std": std.tolist(),
         "iterations_alpha1_mean": float(n[:, :, one].mean()),
         "best_alpha": alphas[best], "speedup_percent": 100.0 * (1.0 - mean[best]),
@@ -102,6 +105,8 @@ def main(argv=None):
     ap.add_argument("--fields", type=int, default=1)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--alphas", default=None, help="comma-separated alpha values")
+    ap.add_argument("--form", type=int, default=0,
+                    help="red-black operator: 0 Eq. redblack, 1 Eq. redblack1, 2 row-scaled")
     args = ap.parse_args(argv)
     lattice = tuple(int(v) for v in args.lattice.split(","))
     alphas = [float(a) for a in args.alphas.split(",")] if args.alphas else None
@@ -109,7 +114,7 @@ def main(argv=None):
     out = []
     for r in rows:
         res = scan(TABLE1_ROWS[r], lattice=lattice, alphas=alphas, fields=args.fields,
-                   tol=args.tol)
+                   tol=args.tol, form=args.form)
         print(json.dumps(res), flush=True)
         out.append(res)
     return out

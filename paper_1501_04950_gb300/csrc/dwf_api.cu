@@ -42,7 +42,8 @@ struct MatSet {
   int Ls = 0;
   std::vector<double> host;
   void* dev[2] = {nullptr, nullptr};  // [0] double, [1] float
-  enum { K = 0, KT = 1, IINV = 2, IINVT = 3, IFULL = 4, BT = 5, NMAT = 6 };
+  // IT = I^T, SI = S I and SIT = (S I)^T for the operator forms of Eq. redblack1
+  enum { K = 0, KT = 1, IINV = 2, IINVT = 3, IFULL = 4, BT = 5, IT = 6, SI = 7, SIT = 8, NMAT = 9 };
   size_t mat_off(int which) const { return (size_t)which * 2 * Ls * Ls; }
   size_t bdiag_off() const { return (size_t)NMAT * 2 * Ls * Ls; }
   size_t boff_off() const { return bdiag_off() + 2 * (size_t)Ls; }
@@ -281,8 +282,16 @@ int build_matset(dwf_ctx* h, double alpha, double m, MatSet** out) {
     if (!invert(I, Ls, Iinv))
       return fail(h, DWF_ERR_INVALID_ARG, "the site-local matrix I = (4+M5)B + C is singular");
     std::vector<double> K = matmul(Bm[ch], Iinv, Ls);
+    // S I: row s of I scaled by 1/(b_s + c_s) where that coefficient exceeds one
+    std::vector<double> SI = I;
+    for (int s = 0; s < Ls; s++) {
+      const double a = h->b[s] + h->c[s];
+      if (a > 1.0)
+        for (int q = 0; q < Ls; q++) SI[(size_t)s * Ls + q] /= a;
+    }
     std::vector<double> mats[MatSet::NMAT] = {K, transpose(K, Ls), Iinv, transpose(Iinv, Ls), I,
-                                              transpose(Bm[ch], Ls)};
+                                              transpose(Bm[ch], Ls), transpose(I, Ls), SI,
+                                              transpose(SI, Ls)};
     for (int w = 0; w < MatSet::NMAT; w++)
       std::copy(mats[w].begin(), mats[w].end(), ms.host.begin() + ms.mat_off(w) + ch * LL);
     // cyclic bidiagonal form of B
@@ -508,6 +517,26 @@ int apply_dbb_dag(dwf_ctx* h, const CoefView& cv, int prec, void* out, const voi
   return apply_dbb_dag_hat(h, cv, prec, out, in, tmp_blk, tmp_red, nrhs, norm, s);
 }
 
+// out = L in for the site-local dense matrix L = MatSet matrix `which` of each
+// right-hand side (generic local kernel), optional fused |out|^2.
+int apply_local_dense(dwf_ctx* h, const CoefView& cv, int prec, int which, void* out,
+                      const void* in, int nrhs, const Reduce* norm, cudaStream_t s) {
+  LocalLaunch L{};
+  L.prec = prec;
+  L.out = out;
+  L.in = in;
+  L.stride = field_bytes(h->g, prec);
+  L.nrhs = nrhs;
+  L.m = cv.ptr(prec, cv.layout->mat_off(which));
+  L.c = 1.0;
+  L.red = norm;
+  L.prog = hop2::PR_NONE;
+  L.cstride = cv.cstride;
+  L.active = cv.active;
+  KLAUNCH(h, launch_local(h->g, L, s));
+  return DWF_OK;
+}
+
 // (out0, out1) = D_alpha(ms) (in0, in1), FP64 internal halves by parity.
 int apply_dalpha_halves(dwf_ctx* h, const MatSet& ms, void* out[2], const void* in[2], cudaStream_t s) {
   const size_t st = field_bytes(h->g, P64);
@@ -690,6 +719,19 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
     return DWF_OK;
   };
   if ((rc = push_active())) return rc;
+  // Operator form (Sec. 3): M = L D_bb with L = 1, I (Eq. redblack1) or S I (row scaled)
+  const int form = h->opt.schur_form;
+  const int Lw = form == DWF_SCHUR_ROWSCALED ? MatSet::SI : MatSet::IFULL;
+  const int LTw = form == DWF_SCHUR_ROWSCALED ? MatSet::SIT : MatSet::IT;
+  void *tb2 = nullptr, *t64b = nullptr;
+  if (form != DWF_SCHUR_PRECOND) {
+    if ((rc = get_ws(h, "tb2_" + std::to_string(prec), fi * nb, &tb2)) ||
+        (rc = get_ws(h, "t64b", f64 * nb, &t64b)))
+      return rc;
+    // right-hand side L r'_b
+    if ((rc = apply_local_dense(h, cv, P64, Lw, t64b, W.b_hi, nb, nullptr, s))) return rc;
+    CUCHK(h, cudaMemcpyAsync(W.b_hi, t64b, f64 * nb, cudaMemcpyDeviceToDevice, s));
+  }
   CUCHK(h, cudaMemsetAsync(W.x_hi, 0, f64 * nb, s));
   CUCHK(h, cudaMemsetAsync(W.xlo, 0, fx * nb, s));
   CUCHK(h, cudaMemsetAsync(W.p, 0, fi * nb, s));
@@ -713,7 +755,8 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
   }
   if ((rc = push_active())) return rc;
   const int Ls = h->g.Ls;
-  const bool fused = h->fused_cg && !g_disable_tuned && (Ls == 8 || Ls == 12 || Ls == 16);
+  const bool fused = form == DWF_SCHUR_PRECOND && h->fused_cg && !g_disable_tuned &&
+                     (Ls == 8 || Ls == 12 || Ls == 16);
   if (fused && (rc = apply_hat(h, cv, prec, W.tb, W.r, nb, s))) return rc;
 
   auto enqueue_fused = [&](int cur, bool first) -> int {
@@ -761,12 +804,22 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
     const int nxt = 1 - cur;
     int r;
     if ((r = timer_mark(h, s, true, 1))) return r;
-    if ((r = apply_dbb_dag(h, cv, prec, W.z, W.r, W.tr, W.tb, nb, &red_zz[nxt], s))) return r;
+    if (form != DWF_SCHUR_PRECOND) {  // z = D_bb^+ L^T r
+      if ((r = apply_local_dense(h, cv, prec, LTw, tb2, W.r, nb, nullptr, s))) return r;
+      if ((r = apply_dbb_dag(h, cv, prec, W.z, tb2, W.tr, W.tb, nb, &red_zz[nxt], s))) return r;
+    } else if ((r = apply_dbb_dag(h, cv, prec, W.z, W.r, W.tr, W.tb, nb, &red_zz[nxt], s))) {
+      return r;
+    }
     if ((r = timer_mark(h, s, false, 1))) return r;
     KLAUNCH(h, launch_p_update(h->g, prec, W.p, W.z, h->scal + (nxt ? S_ZZ1 : S_ZZ0),
                                h->scal + (cur ? S_ZZ1 : S_ZZ0), kScal, nb, fi, s, h->d_active));
     if ((r = timer_mark(h, s, true, 0))) return r;
-    if ((r = apply_dbb(h, cv, prec, W.w, W.p, W.tr, nb, &red_ww, s))) return r;
+    if (form != DWF_SCHUR_PRECOND) {  // w = L D_bb p
+      if ((r = apply_dbb(h, cv, prec, tb2, W.p, W.tr, nb, nullptr, s))) return r;
+      if ((r = apply_local_dense(h, cv, prec, Lw, W.w, tb2, nb, &red_ww, s))) return r;
+    } else if ((r = apply_dbb(h, cv, prec, W.w, W.p, W.tr, nb, &red_ww, s))) {
+      return r;
+    }
     if ((r = timer_mark(h, s, false, 0))) return r;
     KLAUNCH(h, launch_xr_update(h->g, prec, xprec, W.xlo, W.r, W.p, W.w,
                                 h->scal + (nxt ? S_ZZ1 : S_ZZ0), h->scal + S_WW, kScal, nb, fx, fi,
@@ -858,7 +911,13 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
         return rc;
       }
       KLAUNCH(h, launch_accumulate64(h->g, W.x_hi, xprec, W.xlo, 1, nb, f64, fx, s, h->d_active));
-      if ((rc = apply_dbb(h, cv, P64, W.t64, W.x_hi, W.t64r, nb, nullptr, s))) {
+      if (form != DWF_SCHUR_PRECOND) {
+        if ((rc = apply_dbb(h, cv, P64, t64b, W.x_hi, W.t64r, nb, nullptr, s)) ||
+            (rc = apply_local_dense(h, cv, P64, Lw, W.t64, t64b, nb, nullptr, s))) {
+          cleanup();
+          return rc;
+        }
+      } else if ((rc = apply_dbb(h, cv, P64, W.t64, W.x_hi, W.t64r, nb, nullptr, s))) {
         cleanup();
         return rc;
       }
@@ -1166,6 +1225,7 @@ int dwf_default_options(dwf_options* opt) {
   opt->profile = 0;
   opt->graph = 1;
   opt->rhs_block = 0;
+  opt->schur_form = DWF_SCHUR_PRECOND;
   return DWF_OK;
 }
 
@@ -1197,6 +1257,10 @@ int dwf_create(dwf_handle* out, const int lattice[4], int Ls, double M5, double 
   if (h->opt.bc_t != 1 && h->opt.bc_t != -1) {
     delete h;
     return fail(nullptr, DWF_ERR_INVALID_ARG, "bc_t must be +1 or -1");
+  }
+  if (h->opt.schur_form < DWF_SCHUR_PRECOND || h->opt.schur_form > DWF_SCHUR_ROWSCALED) {
+    delete h;
+    return fail(nullptr, DWF_ERR_INVALID_ARG, "schur_form must be 0, 1 or 2");
   }
   if (!valid_prec(h->opt.precision_inner) || (h->opt.rb_parity != 0 && h->opt.rb_parity != 1)) {
     delete h;

@@ -20,6 +20,7 @@ DWF_OK = 0
 DWF_ERR_NOT_CONVERGED = 4
 FP64, FP32, FP16, BF16 = 0, 1, 2, 3
 SOLVER_RELIABLE, SOLVER_DEFECT, SOLVER_FP64 = 0, 1, 2
+SCHUR_PRECOND, SCHUR_PLAIN, SCHUR_ROWSCALED = 0, 1, 2
 ERRORS = {1: "DWF_ERR_INVALID_ARG", 2: "DWF_ERR_CUDA", 3: "DWF_ERR_OOM",
           4: "DWF_ERR_NOT_CONVERGED", 5: "DWF_ERR_BREAKDOWN", 6: "DWF_ERR_TIMEOUT",
           7: "DWF_ERR_STATE"}
@@ -30,7 +31,8 @@ class Options(ctypes.Structure):
                 ("bc_t", ctypes.c_int), ("rel_tol", ctypes.c_double), ("maxiter", ctypes.c_int),
                 ("reliable_delta", ctypes.c_double), ("solver", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("profile", ctypes.c_int),
-                ("graph", ctypes.c_int), ("rhs_block", ctypes.c_int)]
+                ("graph", ctypes.c_int), ("rhs_block", ctypes.c_int),
+                ("schur_form", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

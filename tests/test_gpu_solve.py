@@ -147,3 +147,27 @@ def test_batched_mixed_alpha_16bit(prec):
     assert all(x["true_resid"] <= 1e-10 for x in st)
     for k in range(6):
         assert np.abs(p[k] - p[k + 6]).max() / np.abs(p[k]).max() < 1e-7
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_schur_forms(form):
+    """Eq. redblack1 (form 1) and its row-scaled form (form 2), Sec. 3: the
+    propagator equals the oracle's, each operator's own residual reaches 1e-10,
+    and plain FP64 CG takes the oracle's CGNR iteration count for that operator
+    (the conditioning is the operator's, not the kernels')."""
+    from synthetic import gauge_field, zolotarev_mobius
+    L = (4, 2, 2, 4)
+    Ls = 6
+    b, c, _, _ = zolotarev_mobius(Ls, 0.05, 6.0)
+    sysm = O.DWFSystem(L, Ls, -1.8, 0.1, 1.0, b, c, gauge_field(L, 0.3, seed=0))
+    src = gaussian_source4d(L, seed=1)
+    ref = O.solve_propagator(sysm, src, tol=1e-10, form=form)
+    prop, _, st = _solve(sysm, src, solver=2, schur_form=form, check_every=2)
+    err = np.abs(prop - ref["z1"]).max() / np.abs(ref["z1"]).max()
+    print("form %d: GPU FP64 %d iterations, oracle %d; z1 err %.1e"
+          % (form, st[0]["iterations"], ref["iterations"], err))
+    assert st[0]["true_resid"] <= 1e-10 and err < 1e-7
+    assert abs(st[0]["iterations"] - ref["iterations"]) <= max(4, 0.03 * ref["iterations"])
+    prop2, _, st2 = _solve(sysm, src, schur_form=form)
+    assert st2[0]["true_resid"] <= 1e-10
+    assert np.abs(prop2 - ref["z1"]).max() / np.abs(ref["z1"]).max() < 1e-7

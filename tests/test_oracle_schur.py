@@ -119,3 +119,45 @@ def test_zolotarev_propagator_is_order_independent():
     perm = np.array([2, 0, 3, 1])
     r2 = O.solve_propagator(_sys(b[perm], c[perm], 1.0, m=0.05), src, tol=1e-13)
     assert np.abs(r1["z1"] - r2["z1"]).max() / np.abs(r1["z1"]).max() < 1e-10
+
+
+def test_row_scale_factors():
+    """S of the row-scaled Eq. redblack1: 1/(b_s + c_s) where that exceeds one."""
+    sys = _sys(np.array([1.5, 0.4, 1.0, 2.0]), np.array([0.5, 0.2, 0.0, -0.5]), 1.0)
+    assert np.allclose(sys.row_scale(), [0.5, 1.0, 1.0, 1.0 / 1.5])
+
+
+@pytest.mark.parametrize("form", [1, 2])
+def test_redblack1_forms(form):
+    """Eq. redblack1 equals I_bb times Eq. redblack (I_bb - D_br I^-1 D_rb =
+    I_bb (1 - I^-1 D_br I^-1 D_rb)); the row-scaled form is S times it; each
+    adjoint is the adjoint."""
+    b, c, _, _ = zolotarev_mobius(6, 0.05, 6.0)
+    sys = _sys(b, c, 0.8, L=(2, 2, 4, 2))
+    op, op_dag, left = sys.schur_operator(form)
+    u = gaussian_half5d(sys.lattice, 6, seed=3)
+    v = gaussian_half5d(sys.lattice, 6, seed=4)
+    want = sys.apply_local_matrix(sys.local_matrix(), sys.dbb(v))
+    if form == 2:
+        want = sys.row_scale().reshape(6, 1, 1, 1) * want
+    assert np.abs(op(v) - want).max() / np.abs(want).max() < 1e-13
+    lhs = np.vdot(u, op(v))
+    rhs = np.vdot(op_dag(u), v)
+    assert abs(lhs - rhs) / abs(lhs) < 1e-13
+
+
+def test_forms_share_the_solution():
+    """All three operators of Sec. 3 solve for the same psi (hence z_1), which the
+    dense LU solve of the full 5D system pins for form 0."""
+    b, c, _, _ = zolotarev_mobius(4, 0.05, 6.0)
+    sys = _sys(b, c, 1.25, m=0.06)
+    src = gaussian_source4d(L2, seed=1)
+    ref = O.solve_propagator(sys, src, tol=1e-12)
+    n = 4 * 16 * 12
+    D = dense_operator(lambda v: O.dalpha(v, sys.U, sys.M5, b, c, sys.alpha, sys.m, sys.bc_t),
+                       n, ref["rhs"].shape)
+    psi = np.linalg.solve(D, ref["rhs"].reshape(n)).reshape(ref["rhs"].shape)
+    for form in (1, 2):
+        res = O.solve_propagator(sys, src, tol=1e-12, form=form)
+        assert res["true_resid"] <= 1e-12
+        assert np.abs(res["psi"] - psi).max() / np.abs(psi).max() < 1e-9
