@@ -210,6 +210,18 @@ int dwf_apply_dalpha(dwf_handle h, double* out_full, const double* in_full, doub
 int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* sol5d, int nrhs,
                    const double* alphas, dwf_stats* stats, dwf_stream s);
 
+/* The 4D overlap operator D_OV(m) = 1/2 [(1 + m) + (1 - m) gamma5 eps] of App. A
+ * applied to nrhs 4D fields b, through the 5D system with the two masses of
+ * Eq. tosolve exchanged (App. B): solve D_alpha(1) P z = D_1(m) P b, b = (b_1, 0,
+ * ..., 0), and return out4d = z_1 = D_OV(1)^-1 D_OV(m) b_1 = D_OV(m) b_1.  eps is the
+ * sign-function approximation defined by the handle's b_i, c_i (Eq. polar); the
+ * solve is the mass-1 (Pauli-Villars) system, whatever the handle's m.  Arguments,
+ * layouts, ownership, stream and errors as dwf_cgne_solve (sol5d: optional full
+ * 5D solution psi = P z; stats refer to the mass-1 solve).  The paper has no
+ * separate entry for this: it is the construction of App. A / B run forward. */
+int dwf_apply_overlap(dwf_handle h, const double* src4d, double* out4d, double* sol5d, int nrhs,
+                      const double* alphas, dwf_stats* stats, dwf_stream s);
+
 /* CG on the normal equations of D_bb for a black half-field right-hand side:
  * x = (D_bb^+ D_bb)^-1 phi (canonical device half-fields, FP64), with the
  * handle's solver options.  The inner solve of dwf_cgne_solve and dwf_force. */

@@ -11,7 +11,8 @@ Modules and the passages they follow:
   wilson   D_w(M5), Sec. 2 Eq. wilson (and its adjoint)
   dwf      D_alpha(m), Sec. 2 Eq. mobius1 / Eq. coeff; P (App. A Eq. eqP); A
   schur    I, D_rb, D_br, D_bb and D_bb^+, Sec. 3 Eq. redblack
-  cgne     CG on the normal equations, Sec. 3; propagator Eq. tosolve1, App. B
+  cgne     CG on the normal equations, Sec. 3; propagator Eq. tosolve1, App. B;
+           D_OV(m) b through the mass-exchanged 5D solve
   force    dS/dU for S = phi^+ (D_bb^+ D_bb)^-1 phi (adjoint of Eq. redblack)
   overlap  dense D_OV with the tanh form of eps, App. A Eq. polar / argument
 
@@ -25,7 +26,8 @@ from .wilson import dw, hop
 from .dwf import (a_apply, blocks, dalpha, dalpha_dag, dalpha_generic, mobius_standard,
                   p_apply, p_inverse)
 from .schur import DWFSystem
-from .cgne import cgnr, propagator_rhs, solve_propagator, source_5d, propagator_from_psi
+from .cgne import (cgnr, overlap_apply, propagator_rhs, solve_propagator, source_5d,
+                   propagator_from_psi)
 from .force import action, cg_normal, force_gradient, su3_force, traceless_antihermitian
 from . import overlap
 
@@ -33,7 +35,7 @@ __all__ = [
     "GAMMA", "GAMMA5", "P_MINUS", "P_PLUS", "full_to_half", "half_to_full", "norm2",
     "parity_grid", "shape4", "vdot", "volume", "dw", "hop", "a_apply", "blocks",
     "dalpha", "dalpha_dag", "dalpha_generic", "mobius_standard", "p_apply", "p_inverse",
-    "DWFSystem", "cgnr", "propagator_rhs", "solve_propagator", "source_5d",
+    "DWFSystem", "cgnr", "overlap_apply", "propagator_rhs", "solve_propagator", "source_5d",
     "propagator_from_psi", "action", "cg_normal", "force_gradient", "su3_force",
     "traceless_antihermitian", "overlap",
 ]

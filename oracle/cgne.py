@@ -109,6 +109,23 @@ def solve_propagator(sys: DWFSystem, src4d, tol=1e-10, maxiter=100000, form=0):
     }
 
 
+def overlap_apply(sys: DWFSystem, src4d, tol=1e-12, maxiter=100000):
+    """D_OV(m) b_1 from the 5D system (App. A / App. B with the masses exchanged).
+
+    Eq. tosolve gives z_1 = D_OV(m)^-1 D_OV(1) b_1 for D_alpha(m) P z = D_1(1) P b,
+    and D_OV(1) = 1.  Solving instead D_alpha(1) P z = D_1(m) P b gives
+    z_1 = D_OV(1)^-1 D_OV(m) b_1 = D_OV(m) b_1: the 4D overlap operator applied
+    through one red-black solve at mass 1 (the Pauli-Villars system).
+    Returns (z_1, iterations, Schur true residual)."""
+    sys1 = DWFSystem(sys.lattice, sys.Ls, sys.M5, 1.0, sys.alpha, sys.b, sys.c, sys.U,
+                     bc_t=sys.bc_t, black_parity=sys.black_parity)
+    b5 = source_5d(src4d, sys.Ls)
+    rhs = dalpha(p_apply(b5), sys.U, sys.M5, sys.b, sys.c, 1.0, sys.m, sys.bc_t)
+    xb, it, res = cgnr(sys1.dbb, sys1.dbb_dag, sys1.schur_rhs(rhs), tol=tol, maxiter=maxiter)
+    psi = sys1.reconstruct(xb, rhs)
+    return p_inverse(psi)[0], it, res
+
+
 def propagator_from_psi(psi):
     """z_1 = P_- psi_1 + P_+ psi_Ls from a full 5D solution psi = P z."""
     return p_inverse(psi)[0]

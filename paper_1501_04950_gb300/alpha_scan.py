@@ -38,26 +38,48 @@ TABLE1_ROWS = [
 ]
 
 
-def row_coefficients(row):
-    from synthetic import zolotarev_mobius
+ORDERS = ("concave", "ascending", "descending", "random")
+
+
+def order_coefficients(a, order):
+    """Place the Zolotarev coefficients a_i along the 5th dimension (Sec. 3): concave
+    (smallest at s = 1 and Ls, largest in the centre), ascending, descending, or a
+    seeded random permutation."""
+    from synthetic import concave_order
+    a = np.sort(np.asarray(a, dtype=np.float64))
+    if order == "concave":
+        return concave_order(a)
+    if order == "ascending":
+        return a
+    if order == "descending":
+        return a[::-1].copy()
+    if order == "random":
+        return np.random.default_rng(7).permutation(a)
+    raise ValueError("order must be one of %s" % (ORDERS,))
+
+
+def row_coefficients(row, order="concave"):
+    from synthetic import zolotarev_sign_coefficients
     mass, Ls, b, c = row
     if b is None:
-        bb, cc, _, _ = zolotarev_mobius(Ls, 0.05, 6.0)
-        return mass, Ls, bb, cc
+        a, _ = zolotarev_sign_coefficients(Ls, 0.05, 6.0)
+        a = order_coefficients(a, order)
+        return mass, Ls, 0.5 * (a + 1.0), 0.5 * (a - 1.0)
     return mass, Ls, np.full(Ls, float(b)), np.full(Ls, float(c))
 
 
 def scan(row, lattice=(16, 16, 16, 32), alphas=None, fields=1, eps=0.5, M5=-1.8, tol=1e-8,
-         precision=None, sources=12, device="cuda", form=0):
+         precision=None, sources=12, device="cuda", form=0, order="concave"):
     """Run the scan for one row; returns a dict of per-alpha ratio statistics.
 
     form selects the red-black operator of Sec. 3 (dwf.SCHUR_*: 0 Eq. redblack,
-    1 Eq. redblack1, 2 Eq. redblack1 with scaled rows)."""
+    1 Eq. redblack1, 2 Eq. redblack1 with scaled rows); order places the
+    Zolotarev coefficients of a Zolotarev row (ORDERS)."""
     import torch
     from synthetic import gauge_field, point_source4d
     from . import dwf
 
-    mass, Ls, b, c = row_coefficients(row)
+    mass, Ls, b, c = row_coefficients(row, order)
     if alphas is None:
         alphas = [round(0.3 + 0.05 * k, 2) for k in range(19)]  # 0.3 .. 1.2
     alphas = list(alphas)
@@ -89,7 +111,7 @@ def scan(row, lattice=(16, 16, 16, 32), alphas=None, fields=1, eps=0.5, M5=-1.8,
     return {
         "row": {"mass": mass, "Ls": Ls, "b": "zolotarev" if row[2] is None else row[2],
                 "c": "zolotarev" if row[3] is None else row[3]},
-        "form": form, "lattice": list(lattice), "fields": fields, "sources": len(pts), "tol": tol,
+        "form": form, "order": order if row[2] is None else None, "lattice": list(lattice), "fields": fields, "sources": len(pts), "tol": tol,
         "alphas": alphas, "ratio_mean": mean.tolist(), "ratio_std": std.tolist(),
         "iterations_alpha1_mean": float(n[:, :, one].mean()),
         "best_alpha": alphas[best], "speedup_percent": 100.0 * (1.0 - mean[best]),
@@ -107,6 +129,8 @@ def main(argv=None):
     ap.add_argument("--alphas", default=None, help="comma-separated alpha values")
     ap.add_argument("--form", type=int, default=0,
                     help="red-black operator: 0 Eq. redblack, 1 Eq. redblack1, 2 row-scaled")
+    ap.add_argument("--order", default="concave", choices=ORDERS,
+                    help="placement of the Zolotarev coefficients along the 5th dimension")
     args = ap.parse_args(argv)
     lattice = tuple(int(v) for v in args.lattice.split(","))
     alphas = [float(a) for a in args.alphas.split(",")] if args.alphas else None
@@ -114,7 +138,7 @@ def main(argv=None):
     out = []
     for r in rows:
         res = scan(TABLE1_ROWS[r], lattice=lattice, alphas=alphas, fields=args.fields,
-                   tol=args.tol, form=args.form)
+                   tol=args.tol, form=args.form, order=args.order)
         print(json.dumps(res), flush=True)
         out.append(res)
     return out

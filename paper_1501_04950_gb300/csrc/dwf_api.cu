@@ -1478,8 +1478,28 @@ int dwf_solve_normal(dwf_handle h, double* x_half, const double* phi_half, dwf_s
   return rc;
 }
 
+// Red-black solves of D_alpha(solve_m) P z = D_1(rhs_m) P b for nrhs sources,
+// z_1 -> prop4d: the propagator (solve_m = m, rhs_m = 1) or D_OV(m) b
+// (solve_m = 1, rhs_m = m).
+static int solve_5d(dwf_ctx* h, const double* src4d, double* prop4d, double* sol5d, int nrhs,
+                    const double* alphas, dwf_stats* stats, dwf_stream s, double solve_m,
+                    double rhs_m);
+
 int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* sol5d, int nrhs,
                    const double* alphas, dwf_stats* stats, dwf_stream s) {
+  if (!h) return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  return solve_5d(h, src4d, prop4d, sol5d, nrhs, alphas, stats, s, h->m, 1.0);
+}
+
+int dwf_apply_overlap(dwf_handle h, const double* src4d, double* out4d, double* sol5d, int nrhs,
+                      const double* alphas, dwf_stats* stats, dwf_stream s) {
+  if (!h) return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  return solve_5d(h, src4d, out4d, sol5d, nrhs, alphas, stats, s, 1.0, h->m);
+}
+
+static int solve_5d(dwf_ctx* h, const double* src4d, double* prop4d, double* sol5d, int nrhs,
+                    const double* alphas, dwf_stats* stats, dwf_stream s, double solve_m,
+                    double rhs_m) {
   if (!h || !src4d || !prop4d || nrhs < 1) return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
   if (!h->gauge_loaded) return fail(h, DWF_ERR_STATE, "gauge field not loaded");
   // all solver work runs on the handle's stream, after the caller's stream
@@ -1495,9 +1515,9 @@ int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* so
   solver_params(h, &prec, &delta, &restart);
   std::vector<MatSet*> ms(nrhs);
   for (int k = 0; k < nrhs; k++)
-    if ((rc = build_matset(h, alphas ? alphas[k] : h->alpha, h->m, &ms[k]))) return rc;
+    if ((rc = build_matset(h, alphas ? alphas[k] : h->alpha, solve_m, &ms[k]))) return rc;
   MatSet* rhs_set;
-  if ((rc = build_matset(h, 1.0, 1.0, &rhs_set))) return rc;
+  if ((rc = build_matset(h, 1.0, rhs_m, &rhs_set))) return rc;
   int nb = 1;
   if ((rc = choose_rhs_block(h, nrhs, prec, st, &nb))) return rc;
   if ((rc = ensure_reduce(h, nb))) return rc;

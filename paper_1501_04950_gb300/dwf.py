@@ -51,7 +51,7 @@ EXPORTS = [
     "dwf_default_options", "dwf_create", "dwf_destroy", "dwf_last_error", "dwf_field_bytes",
     "dwf_load_gauge", "dwf_pack_half", "dwf_unpack_half", "dwf_apply_Dbb", "dwf_apply_Dbb_dag",
     "dwf_apply_dalpha", "dwf_cgne_solve", "dwf_solve_normal", "dwf_force",
-    "dwf_apply_Dbb_noalloc",
+    "dwf_apply_Dbb_noalloc", "dwf_apply_overlap",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "dwf_apply_Dbb_noalloc": (I, [P, P, P, I, I, P]),
         "dwf_apply_dalpha": (I, [P, P, P, D, D, P]),
         "dwf_cgne_solve": (I, [P, P, P, P, I, ctypes.POINTER(D), ctypes.POINTER(Stats), P]),
+        "dwf_apply_overlap": (I, [P, P, P, P, I, ctypes.POINTER(D), ctypes.POINTER(Stats), P]),
         "dwf_solve_normal": (I, [P, P, P, ctypes.POINTER(Stats), P]),
         "dwf_force": (I, [P, P, P, P, I, P]),
     }
@@ -198,6 +199,16 @@ class DWF:
         rc = self.lib.dwf_cgne_solve(self.h, _ptr(src4d), _ptr(prop4d), _ptr(sol5d), nrhs, al, st,
                                      _stream())
         self._check(rc, allow=(DWF_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+        return [s.as_dict() for s in st]
+
+    def apply_overlap(self, src4d, out4d, sol5d=None, nrhs=1, alphas=None):
+        """out4d = D_OV(m) src4d through the mass-exchanged 5D solve (dwf_apply_overlap)."""
+        st = (Stats * nrhs)()
+        al = None
+        if alphas is not None:
+            al = (ctypes.c_double * nrhs)(*[float(a) for a in alphas])
+        self._check(self.lib.dwf_apply_overlap(self.h, _ptr(src4d), _ptr(out4d), _ptr(sol5d), nrhs,
+                                               al, st, _stream()))
         return [s.as_dict() for s in st]
 
     def solve_normal(self, x_half, phi_half):

@@ -22,3 +22,19 @@ def test_small_scan():
     assert res["ratio_mean"][k] == 1.0 and res["ratio_std"][k] == 0.0
     assert all(r > 0 for r in res["ratio_mean"])
     assert res["iterations_alpha1_mean"] > 0
+
+
+def test_zolotarev_orderings():
+    """Every ordering is a permutation of the same a_i; concave puts the smallest
+    at both ends and the largest in the centre (Sec. 3); b - c = 1, b + c = a."""
+    from synthetic import zolotarev_mobius
+    m, Ls, b, c = alpha_scan.row_coefficients(alpha_scan.TABLE1_ROWS[7], "concave")
+    bz, cz, _, _ = zolotarev_mobius(Ls, 0.05, 6.0)
+    assert np.allclose(b, bz) and np.allclose(c, cz)
+    a = b + c
+    assert np.argmax(a) in (Ls // 2 - 1, Ls // 2) and min(a[0], a[-1]) == a.min()
+    for order in alpha_scan.ORDERS:
+        _, _, bo, co = alpha_scan.row_coefficients(alpha_scan.TABLE1_ROWS[7], order)
+        assert np.allclose(np.sort(bo + co), np.sort(a)) and np.allclose(bo - co, 1.0)
+    _, _, bo, co = alpha_scan.row_coefficients(alpha_scan.TABLE1_ROWS[7], "ascending")
+    assert np.all(np.diff(bo + co) > 0)

@@ -160,19 +160,28 @@ def test_staged_matches_direct_loads(Ls, prec, monkeypatch):
         assert np.array_equal(outs[0][k], outs[1][k])
 
 
-@pytest.mark.parametrize("prec,tol", [(1, 5e-6), (0, 1e-12)])
-def test_full_size_sampled_parity(prec, tol):
-    """16^3x32, Ls = 16 (the benchmark workload and its launch configuration):
-    the GPU D_bb at 24 sampled black sites against the single-site oracle."""
+@pytest.mark.parametrize("L,prec,tol", [((16, 16, 16, 32), 1, 5e-6), ((16, 16, 16, 32), 0, 1e-12),
+                                         ((32, 32, 32, 64), 1, 5e-6)])
+def test_full_size_sampled_parity(L, prec, tol):
+    """16^3x32, Ls = 16 (the benchmark workload and its launch configuration) and
+    32^3x64, Ls = 16 (16.8M 5D half-sites, the largest batched lattice): the GPU
+    D_bb at 24 sampled black sites against the single-site oracle."""
     import oracle as O
     from oracle.pointwise import PointwiseDbb
     from synthetic import gauge_field
-    L, Ls = (16, 16, 16, 32), 16
+    Ls = 16
     sysm = O.DWFSystem(L, Ls, -1.8, 0.01, 1.0, np.full(Ls, 1.5), np.full(Ls, 0.5),
                        gauge_field(L, 0.5, seed=0))
     op = _op(sysm)
     psi = gaussian_half5d(L, Ls, seed=2)
-    got = _apply(op, psi, prec)
+    x = op.new_field(prec)
+    y = op.new_field(prec)
+    op.pack_half(x, torch.from_numpy(psi).cuda(), prec)
+    op.apply_Dbb(y, x, prec)
+    out = torch.empty(psi.shape, dtype=torch.complex128, device="cuda")
+    op.unpack_half(out, y, prec)
+    torch.cuda.synchronize()
+    del x, y
     pw = PointwiseDbb(sysm)
     rng = np.random.default_rng(7)
     refs, gots = [], []
@@ -180,9 +189,9 @@ def test_full_size_sampled_parity(prec, tol):
         c = tuple(int(rng.integers(0, n)) for n in L)
         if sum(c) % 2 != 0:
             continue
-        lex = c[0] + 16 * (c[1] + 16 * (c[2] + 16 * c[3]))
+        lex = c[0] + L[0] * (c[1] + L[1] * (c[2] + L[2] * c[3]))
         refs.append(pw.dbb_at(psi, c))
-        gots.append(got[:, lex // 2])
+        gots.append(out[:, lex // 2].cpu().numpy())
     refs = np.stack(refs, axis=1)
     gots = np.stack(gots, axis=1)
     rms = np.sqrt((np.abs(refs) ** 2).sum(axis=(-1, -2)).mean())

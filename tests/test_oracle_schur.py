@@ -161,3 +161,18 @@ def test_forms_share_the_solution():
         res = O.solve_propagator(sys, src, tol=1e-12, form=form)
         assert res["true_resid"] <= 1e-12
         assert np.abs(res["psi"] - psi).max() / np.abs(psi).max() < 1e-9
+
+
+@pytest.mark.parametrize("name,alpha", [("mobius", 1.0), ("varying_b_minus_c_1", 1.4), ("shamir", 0.7)])
+def test_overlap_apply_equals_dense_overlap(name, alpha):
+    """D_OV(m) b_1 from the mass-exchanged 5D solve equals the dense tanh-form
+    overlap operator of App. A applied to b_1 (2^4 lattice)."""
+    b, c = OVERLAP_SETS[name]
+    m = 0.05
+    sys = _sys(b, c, alpha, m=m)
+    src = gaussian_source4d(L2, seed=1)
+    z1, it, res = O.overlap_apply(sys, src, tol=1e-13)
+    dov = overlap_operator(dense_dw(sys.U, L2, sys.M5), dense_gamma5(L2), b, c, m)
+    want = (dov @ src.reshape(-1)).reshape(src.shape)
+    assert res <= 1e-13
+    assert np.abs(z1 - want).max() / np.abs(want).max() < 1e-11
