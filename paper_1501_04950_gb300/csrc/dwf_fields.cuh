@@ -194,13 +194,18 @@ struct Store16 {
     for (int q = 0; q < 6; q++)
       o[q] = cmake(sc * to_f((uint16_t)(w[q] & 0xffffu)), sc * to_f((uint16_t)(w[q] >> 16)));
   }
+  // Per-site scale from the largest |component|.  Below the smallest normal float
+  // (subnormal or zero, e.g. the far tail of a point-source solve) 1/max would
+  // overflow to inf: such a site keeps scale 1, and its components, far below
+  // 16-bit resolution, store as zero.  A NaN component still stores as NaN.
+  __device__ static float scale_of(float mx) { return mx >= 1.17549435e-38f ? mx : 1.f; }
   // o <- what store() followed by load() gives back, computed in registers (a
   // kernel must not re-read through __ldg what it wrote itself).
   __device__ static void quantize(Spinor<float>& o) {
     float mx = 0.f;
 #pragma unroll
     for (int k = 0; k < 12; k++) mx = fmaxf(mx, fmaxf(fabsf(o.c[k].re), fabsf(o.c[k].im)));
-    const float sc = mx > 0.f ? mx : 1.f;
+    const float sc = scale_of(mx);
     const float inv = 1.f / sc;
 #pragma unroll
     for (int k = 0; k < 12; k++)
@@ -211,7 +216,7 @@ struct Store16 {
     float mx = 0.f;
 #pragma unroll
     for (int k = 0; k < 12; k++) mx = fmaxf(mx, fmaxf(fabsf(o.c[k].re), fabsf(o.c[k].im)));
-    const float sc = mx > 0.f ? mx : 1.f;
+    const float sc = scale_of(mx);
     const float inv = 1.f / sc;
 #pragma unroll
     for (int k = 0; k < 3; k++) {

@@ -197,3 +197,35 @@ def test_full_size_sampled_parity(L, prec, tol):
     rms = np.sqrt((np.abs(refs) ** 2).sum(axis=(-1, -2)).mean())
     d = np.sqrt((np.abs(gots - refs) ** 2).sum(axis=(-1, -2)))
     assert d.max() / rms <= tol, d.max() / rms
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+def test_16bit_store_subnormal_sites(prec):
+    """A 5D site whose components are all below the smallest normal float (the far
+    tail of a point-source solve) keeps scale 1 instead of overflowing its 1/max
+    scale: it stores as zero in FP16 and as the (subnormal) value in BF16, whose
+    exponent range is FP32's; normal sites keep their 16-bit accuracy, and D_bb of
+    such a field stays finite."""
+    L, Ls = (4, 4, 4, 4), 8
+    sysm = make_case(L, Ls, "mobius")
+    op = _op(sysm)
+    psi = gaussian_half5d(L, Ls, seed=6)
+    psi[3, 5] *= 1e-40          # subnormal in FP32
+    psi[4, 7] *= 3e-36          # small but normal
+    x = op.new_field(prec)
+    op.pack_half(x, torch.from_numpy(psi).cuda(), prec)
+    back = torch.empty(psi.shape, dtype=torch.complex128, device="cuda")
+    op.unpack_half(back, x, prec)
+    b = back.cpu().numpy()
+    assert np.isfinite(b).all()
+    assert np.abs(b[3, 5]).max() <= (0.0 if prec == 2 else 1.2e-38)
+    tol = 2e-3 if prec == 2 else 1e-2
+    assert np.abs(b[4, 7] - psi[4, 7]).max() <= tol * np.abs(psi[4, 7]).max()
+    mask = np.ones(psi.shape[:2], dtype=bool)
+    mask[3, 5] = mask[4, 7] = False
+    assert np.abs(b[mask] - psi[mask]).max() <= tol * np.abs(psi).max()
+    y = op.new_field(prec)
+    op.apply_Dbb(y, x, prec)
+    out = torch.empty_like(back)
+    op.unpack_half(out, y, prec)
+    assert torch.isfinite(out).all()
