@@ -53,6 +53,21 @@ def workload_name(alpha):
             "Gaussian source; mixed FP32/FP64 CGNE to 1e-10" % alpha)
 
 
+def replica_throughput(moved, seconds, world, device=None):
+    """Whole-job GB/s of N independent replicas (one per rank, no data-path
+    collective): the bytes all ranks moved divided by the slowest rank's time
+    (sum and max over ranks).  world = 1: moved / seconds."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        m = torch.tensor([float(moved)], dtype=torch.float64, device=device)
+        t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+        dist.all_reduce(m, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        moved, seconds = float(m.item()), float(t.item())
+    return moved / seconds / 1e9
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -395,11 +410,12 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    dt = maxtime(e0.elapsed_time(e1) / 1e3)
+    dt_local = e0.elapsed_time(e1) / 1e3
+    dt = maxtime(dt_local)
     applies = sum(s["applies"] + s["applies_dag"] for s in stats)
     applies64 = sum(s["applies_fp64"] for s in stats)
     moved = applies * b_inner + applies64 * b_fp64
-    value = moved * world / dt / 1e9
+    value = replica_throughput(moved, dt_local, world, dev)
     apply_ms = sum(s["apply_ms"] for s in stats)
     n_apply = sum(s["applies"] for s in stats)
     achieved = n_apply * b_inner / (apply_ms / 1e3) / 1e9 if apply_ms > 0 else None
@@ -414,9 +430,10 @@ def main():
     for _ in range(args.steps):
         e2e_stats += op.cgne_solve(src_h, prop_h)
     torch.cuda.synchronize()
-    dt_e2e = maxtime(time.perf_counter() - t0)
+    dt_e2e_local = time.perf_counter() - t0
     moved_e2e = sum((s["applies"] + s["applies_dag"]) * b_inner + s["applies_fp64"] * b_fp64
                     for s in e2e_stats)
+    value_e2e = replica_throughput(moved_e2e, dt_e2e_local, world, dev)
     io_bytes = src_h.numel() * 16
 
     fp64 = None
@@ -484,7 +501,7 @@ def main():
                          "bytes_per_apply": b_inner},
             "alpha_sweep": sweep,
             "cpu_baseline": cpu,
-            "e2e": {"value": moved_e2e * world / dt_e2e / 1e9, "unit": "GB/s",
+            "e2e": {"value": value_e2e, "unit": "GB/s",
                     "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
             "gpu_launches": launches,
             "clocks": clocks,
