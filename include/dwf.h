@@ -9,7 +9,10 @@
  * built on the operator D_alpha(m) of Sec. 2 (Eq. mobius1, Eq. coeff) with the
  * Wilson matrix D_w(M5) of Eq. wilson, and solves D_alpha(m) P z = D_1(1) P b for
  * the 4D propagator z_1 = y_1 (Eq. tosolve1, App. B Eq. tosolve) by conjugate
- * gradient on the normal equations of D_bb (Sec. 3).
+ * gradient on the normal equations of D_bb (Sec. 3).  The same machinery applies
+ * the 4D overlap operator of App. A (dwf_apply_overlap), runs the older red-black
+ * forms of Sec. 3 (dwf_options.schur_form) and gives the fermion force of
+ * S = phi^+ (D_bb^+ D_bb)^-1 phi (dwf_force).
  *
  * Conventions shared by every entry point
  *   - Status: every call returns an int, DWF_OK (0) on success.  On error the
@@ -20,8 +23,9 @@
  *     after a call returns.  The handle owns its gauge copies, matrices and
  *     workspace (device memory allocated by the library).
  *   - Streams: every call is ordered on the given stream (a cudaStream_t; NULL
- *     is the legacy default stream).  Apply calls do not synchronise.
- *     dwf_cgne_solve synchronises the stream internally (convergence polling).
+ *     is the legacy default stream).  Apply calls do not synchronise.  The
+ *     solver calls (dwf_cgne_solve, dwf_apply_overlap, dwf_solve_normal,
+ *     dwf_force without X) synchronise internally (convergence polling).
  *   - Gamma basis: chiral, gamma_k = [[0,-i sigma_k],[i sigma_k,0]],
  *     gamma_4 = [[0,1],[1,0]], gamma5 = diag(1,1,-1,-1); mu = 0..3 <-> x,y,z,t.
  *   - Canonical layouts (complex128 stored as interleaved double pairs, C order):
@@ -204,9 +208,11 @@ int dwf_apply_dalpha(dwf_handle h, double* out_full, const double* in_full, doub
  * The right-hand side is rhs = D_1(1) P b; red-black: r'_b = I^-1(rhs_b - D_br I^-1 rhs_r),
  * CG on D_bb^+ D_bb x = D_bb^+ r'_b to FP64 true residual opt.rel_tol, then
  * psi_r = I^-1 (rhs_r - D_rb psi_b).  Returns DWF_ERR_NOT_CONVERGED if any
- * source misses the tolerance within maxiter iterations, or if three
- * consecutive FP64 residual replacements fail to lower the true residual by
- * 10% (the tolerance is below what the arithmetic can reach). */
+ * source misses the tolerance within maxiter iterations, or if five
+ * consecutive FP64 residual replacements fail to lower its true residual by
+ * 10% (each such replacement restarts its recurrence; five in a row mean the
+ * tolerance is below what the arithmetic can reach), DWF_ERR_BREAKDOWN if a CG
+ * scalar is not finite or |D p|^2 <= 0. */
 int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* sol5d, int nrhs,
                    const double* alphas, dwf_stats* stats, dwf_stream s);
 
@@ -224,7 +230,8 @@ int dwf_apply_overlap(dwf_handle h, const double* src4d, double* out4d, double* 
 
 /* CG on the normal equations of D_bb for a black half-field right-hand side:
  * x = (D_bb^+ D_bb)^-1 phi (canonical device half-fields, FP64), with the
- * handle's solver options.  The inner solve of dwf_cgne_solve and dwf_force. */
+ * handle's solver options (inner precision and FP64 reliable updates of the
+ * normal residual phi - D_bb^+ D_bb x).  The solve inside dwf_force. */
 int dwf_solve_normal(dwf_handle h, double* x_half, const double* phi_half, dwf_stats* stats,
                      dwf_stream s);
 
