@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -102,7 +103,7 @@ class ClockSampler:
     def __init__(self, index=0):
         self.proc = None
         self.index = index
-        self.path = os.path.join(ROOT, "gpurun_out", "bench_clocks.csv")
+        self.path = os.path.join(tempfile.gettempdir(), "dwf_bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)

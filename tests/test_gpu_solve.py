@@ -1,6 +1,6 @@
 """GPU propagator solves against the FP64 oracle.
 
-Every solve must reach the FP64 true Schur residual 1e-10 (BASELINE target);
+Every solve must reach the FP64 true Schur residual 1e-10;
 the 4D propagator error against the oracle's own 1e-12 solve is reported
 (printed) and bounded by 1e-7, a loose multiple of kappa_eff * 1e-10.
 z_1 must not depend on alpha (Sec. 2, Eq. tosolve1).
