@@ -1,0 +1,44 @@
+"""Host-side measurement logic of bench.py (no GPU): the algorithmic byte model,
+the traffic record's source-hash gate and the clock / throttle-reason parsing."""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_byte_model():
+    # two passes, each reading its input spinor and all links once: 120 w_s + 16 r w_g / Ls
+    assert bench.bytes_per_site(4, 4, 16) == 552.0
+    assert bench.bytes_per_site(8, 8, 16) == 1104.0
+    n5 = 16 ** 3 * 32 // 2 * 16
+    assert n5 * bench.bytes_per_site(4, 4, 16) == 578813952.0
+
+
+def test_traffic_record_is_gated_by_source_hash(tmp_path, monkeypatch):
+    rec = {"kernel_hash": bench.kernel_hash(), "dram_bytes_per_apply_full_size": 123}
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "dbb_apply_traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_hash", lambda: rec["kernel_hash"])
+    assert bench.measured_traffic() == 123
+    monkeypatch.setattr(bench, "kernel_hash", lambda: "0" * 16)
+    assert bench.measured_traffic() is None
+
+
+def test_clock_parsing():
+    rows = [
+        "0, 2070, 2070, 980.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1001.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ]
+    c = bench.parse_clock_samples(rows)
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c = bench.parse_clock_samples(["0, 1400, 2070, 700, 0x8, Active, Not Active, Not Active, Not Active"])
+    assert c["reasons"] == ["hw_slowdown"] and c["sm_mhz"] == 1400.0
+    assert bench.parse_clock_samples([]) is None
