@@ -1178,7 +1178,7 @@ int choose_rhs_block(dwf_ctx* h, int nrhs, int prec, cudaStream_t st, int* nb_ou
   double best = 1e300;
   int best_nb = 1, best_tma = saved_tma;
   for (int nb : ok) {
-    for (int tma = 0; tma < 2; tma++) {
+    for (int tma = 0; tma < 1; tma++) {
       h->use_tma = tma;
       if ((rc = apply_dbb(h, view_of(*ms), prec, y, x, t, nb, nullptr, st))) return rc;
       CUCHK(h, cudaEventRecord(e0, st));

@@ -8,38 +8,6 @@ namespace {
 
 constexpr int kBlasThreads = 256;
 
-__device__ void reduce_block(double v, const Reduce& red, int rhs, int nblocks, int bid) {
-  __shared__ double wsum[32];
-  const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if (lane == 0) wsum[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    v = lane < nw ? wsum[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    double* part = red.partial + (size_t)rhs * red.partial_stride;
-    unsigned int ticket = 0;
-    if (lane == 0) {
-      part[bid] = v;
-      __threadfence();
-      ticket = atomicAdd(red.counter + rhs, 1u);
-    }
-    ticket = __shfl_sync(0xffffffffu, ticket, 0);
-    if (ticket == (unsigned)(nblocks - 1)) {
-      __threadfence();
-      double acc = 0.0;
-      for (int b = lane; b < nblocks; b += 32) acc += *((volatile double*)(part + b));
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if (lane == 0) {
-        red.result[(size_t)rhs * red.result_stride] = acc;
-        red.counter[rhs] = 0u;
-      }
-    }
-  }
-}
-
 template <typename T>
 __device__ __forceinline__ double sqd(const Spinor<T>& a) {
   T r = 0;
@@ -222,6 +190,7 @@ __global__ void extract_z1_kernel(const Geom g, double* prop, const void* p0, co
 }
 
 // ---- BLAS-1 -------------------------------------------------------------------
+// One thread per slice pair m (two 5D sites), vector loads of the pair layout.
 
 template <class SPX, class SP>
 __global__ void __launch_bounds__(kBlasThreads) xr_update_kernel(
@@ -235,24 +204,27 @@ __global__ void __launch_bounds__(kBlasThreads) xr_update_kernel(
   const double ad = num[rhs * sstride] / den[rhs * sstride];
   const T a = (T)ad;
   const TX ax = (TX)ad;
+  const int NP = g.N5 >> 1;
   double acc = 0.0;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
-    Spinor<TX> xv;
-    Spinor<T> rv, pv, wv;
-    SPX::load(reinterpret_cast<const char*>(x) + offx, n, g.N5, xv);
-    SP::load(reinterpret_cast<const char*>(r) + off, n, g.N5, rv);
-    SP::load(reinterpret_cast<const char*>(p) + off, n, g.N5, pv);
-    SP::load(reinterpret_cast<const char*>(w) + off, n, g.N5, wv);
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < NP; m += gridDim.x * blockDim.x) {
+    Spinor<TX> xv[2];
+    Spinor<T> rv[2], pv[2], wv[2];
+    SPX::load_pair(reinterpret_cast<const char*>(x) + offx, m, NP, xv[0], xv[1]);
+    SP::load_pair(reinterpret_cast<const char*>(r) + off, m, NP, rv[0], rv[1]);
+    SP::load_pair(reinterpret_cast<const char*>(p) + off, m, NP, pv[0], pv[1]);
+    SP::load_pair(reinterpret_cast<const char*>(w) + off, m, NP, wv[0], wv[1]);
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-      xv.c[k] = cmake(fma(ax, (TX)pv.c[k].re, xv.c[k].re), fma(ax, (TX)pv.c[k].im, xv.c[k].im));
-      rv.c[k] = cmake(fma(-a, wv.c[k].re, rv.c[k].re), fma(-a, wv.c[k].im, rv.c[k].im));
-    }
-    SPX::store(reinterpret_cast<char*>(x) + offx, n, g.N5, xv);
-    SP::store(reinterpret_cast<char*>(r) + off, n, g.N5, rv);
-    acc += sqd(rv);
+    for (int l = 0; l < 2; l++)
+#pragma unroll
+      for (int k = 0; k < 12; k++) {
+        xv[l].c[k] = cmake(fma(ax, (TX)pv[l].c[k].re, xv[l].c[k].re), fma(ax, (TX)pv[l].c[k].im, xv[l].c[k].im));
+        rv[l].c[k] = cmake(fma(-a, wv[l].c[k].re, rv[l].c[k].re), fma(-a, wv[l].c[k].im, rv[l].c[k].im));
+      }
+    SPX::store_pair(reinterpret_cast<char*>(x) + offx, m, NP, xv[0], xv[1]);
+    SP::store_pair(reinterpret_cast<char*>(r) + off, m, NP, rv[0], rv[1]);
+    acc += sqd(rv[0]) + sqd(rv[1]);
   }
-  reduce_block(acc, red, rhs, gridDim.x, blockIdx.x);
+  block_sum_to(acc, red, rhs, gridDim.x, blockIdx.x);
 }
 
 template <class SP>
@@ -264,14 +236,17 @@ __global__ void __launch_bounds__(kBlasThreads) p_update_kernel(
   if (active && !active[rhs]) return;
   const size_t off = rhs * stride;
   const T beta = (T)(num[rhs * sstride] / den[rhs * sstride]);
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
-    Spinor<T> pv, zv;
-    SP::load(reinterpret_cast<const char*>(p) + off, n, g.N5, pv);
-    SP::load(reinterpret_cast<const char*>(z) + off, n, g.N5, zv);
+  const int NP = g.N5 >> 1;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < NP; m += gridDim.x * blockDim.x) {
+    Spinor<T> pv[2], zv[2];
+    SP::load_pair(reinterpret_cast<const char*>(p) + off, m, NP, pv[0], pv[1]);
+    SP::load_pair(reinterpret_cast<const char*>(z) + off, m, NP, zv[0], zv[1]);
 #pragma unroll
-    for (int k = 0; k < 12; k++)
-      pv.c[k] = cmake(fma(beta, pv.c[k].re, zv.c[k].re), fma(beta, pv.c[k].im, zv.c[k].im));
-    SP::store(reinterpret_cast<char*>(p) + off, n, g.N5, pv);
+    for (int l = 0; l < 2; l++)
+#pragma unroll
+      for (int k = 0; k < 12; k++)
+        pv[l].c[k] = cmake(fma(beta, pv[l].c[k].re, zv[l].c[k].re), fma(beta, pv[l].c[k].im, zv[l].c[k].im));
+    SP::store_pair(reinterpret_cast<char*>(p) + off, m, NP, pv[0], pv[1]);
   }
 }
 
@@ -287,26 +262,32 @@ __global__ void __launch_bounds__(kBlasThreads) px_update_kernel(
   const size_t off = rhs * stride, offx = rhs * stride_x;
   const TX a = (TX)a_ptr[(size_t)rhs * sstride];
   const T beta = do_p ? (T)(num[(size_t)rhs * sstride] / den[(size_t)rhs * sstride]) : (T)0;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
-    Spinor<T> pv;
-    Spinor<TX> xv;
-    SP::load(reinterpret_cast<const char*>(p) + off, n, g.N5, pv);
-    SPX::load(reinterpret_cast<const char*>(x) + offx, n, g.N5, xv);
+  const int NP = g.N5 >> 1;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < NP; m += gridDim.x * blockDim.x) {
+    Spinor<T> pv[2];
+    Spinor<TX> xv[2];
+    SP::load_pair(reinterpret_cast<const char*>(p) + off, m, NP, pv[0], pv[1]);
+    SPX::load_pair(reinterpret_cast<const char*>(x) + offx, m, NP, xv[0], xv[1]);
 #pragma unroll
-    for (int k = 0; k < 12; k++)
-      xv.c[k] = cmake(fma(a, (TX)pv.c[k].re, xv.c[k].re), fma(a, (TX)pv.c[k].im, xv.c[k].im));
-    SPX::store(reinterpret_cast<char*>(x) + offx, n, g.N5, xv);
-    if (do_p) {
-      Spinor<T> zv;
-      SP::load(reinterpret_cast<const char*>(z) + off, n, g.N5, zv);
+    for (int l = 0; l < 2; l++)
 #pragma unroll
       for (int k = 0; k < 12; k++)
-        pv.c[k] = cmake(fma(beta, pv.c[k].re, zv.c[k].re), fma(beta, pv.c[k].im, zv.c[k].im));
-      SP::store(reinterpret_cast<char*>(p) + off, n, g.N5, pv);
+        xv[l].c[k] = cmake(fma(a, (TX)pv[l].c[k].re, xv[l].c[k].re), fma(a, (TX)pv[l].c[k].im, xv[l].c[k].im));
+    SPX::store_pair(reinterpret_cast<char*>(x) + offx, m, NP, xv[0], xv[1]);
+    if (do_p) {
+      Spinor<T> zv[2];
+      SP::load_pair(reinterpret_cast<const char*>(z) + off, m, NP, zv[0], zv[1]);
+#pragma unroll
+      for (int l = 0; l < 2; l++)
+#pragma unroll
+        for (int k = 0; k < 12; k++)
+          pv[l].c[k] = cmake(fma(beta, pv[l].c[k].re, zv[l].c[k].re), fma(beta, pv[l].c[k].im, zv[l].c[k].im));
+      SP::store_pair(reinterpret_cast<char*>(p) + off, m, NP, pv[0], pv[1]);
     }
   }
 }
 
+// dst <- src converted; the norm (optional) is that of the stored dst values.
 template <class SPD, class SPS>
 __global__ void __launch_bounds__(kBlasThreads) convert_kernel(
     const Geom g, void* dst, const void* src, size_t sd, size_t ss, Reduce red, int do_norm,
@@ -315,20 +296,24 @@ __global__ void __launch_bounds__(kBlasThreads) convert_kernel(
   using TS = typename SPS::T;
   const int rhs = blockIdx.y;
   if (active && !active[rhs]) return;
+  const int NP = g.N5 >> 1;
   double acc = 0.0;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
-    Spinor<TS> a;
-    SPS::load(reinterpret_cast<const char*>(src) + rhs * ss, n, g.N5, a);
-    Spinor<TD> b;
-    cvt(b, a);
-    SPD::store(reinterpret_cast<char*>(dst) + rhs * sd, n, g.N5, b);
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < NP; m += gridDim.x * blockDim.x) {
+    Spinor<TS> a[2];
+    SPS::load_pair(reinterpret_cast<const char*>(src) + rhs * ss, m, NP, a[0], a[1]);
+    Spinor<TD> b[2];
+    cvt(b[0], a[0]);
+    cvt(b[1], a[1]);
+    SPD::store_pair(reinterpret_cast<char*>(dst) + rhs * sd, m, NP, b[0], b[1]);
     if (do_norm) {
-      Spinor<TD> c;
-      SPD::load(reinterpret_cast<const char*>(dst) + rhs * sd, n, g.N5, c);
-      acc += sqd(c);
+      if constexpr (SPD::kScaled) {
+        SPD::quantize(b[0]);
+        SPD::quantize(b[1]);
+      }
+      acc += sqd(b[0]) + sqd(b[1]);
     }
   }
-  if (do_norm) reduce_block(acc, red, rhs, gridDim.x, blockIdx.x);
+  if (do_norm) block_sum_to(acc, red, rhs, gridDim.x, blockIdx.x);
 }
 
 template <class SPS>
@@ -337,19 +322,23 @@ __global__ void __launch_bounds__(kBlasThreads) accumulate64_kernel(
   using TS = typename SPS::T;
   const int rhs = blockIdx.y;
   if (active && !active[rhs]) return;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
-    Spinor<TS> a;
-    SPS::load(reinterpret_cast<const char*>(src) + rhs * ss, n, g.N5, a);
-    Spinor<double> x;
-    Store64::load(reinterpret_cast<const char*>(x64) + rhs * sd, n, g.N5, x);
+  const int NP = g.N5 >> 1;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < NP; m += gridDim.x * blockDim.x) {
+    Spinor<TS> a[2];
+    SPS::load_pair(reinterpret_cast<const char*>(src) + rhs * ss, m, NP, a[0], a[1]);
+    Spinor<double> x[2];
+    Store64::load_pair(reinterpret_cast<const char*>(x64) + rhs * sd, m, NP, x[0], x[1]);
 #pragma unroll
-    for (int k = 0; k < 12; k++) x.c[k] = cmake(x.c[k].re + (double)a.c[k].re, x.c[k].im + (double)a.c[k].im);
-    Store64::store(reinterpret_cast<char*>(x64) + rhs * sd, n, g.N5, x);
+    for (int l = 0; l < 2; l++)
+#pragma unroll
+      for (int k = 0; k < 12; k++)
+        x[l].c[k] = cmake(x[l].c[k].re + (double)a[l].c[k].re, x[l].c[k].im + (double)a[l].c[k].im);
+    Store64::store_pair(reinterpret_cast<char*>(x64) + rhs * sd, m, NP, x[0], x[1]);
     if (zero_src) {
       Spinor<TS> zz;
 #pragma unroll
       for (int k = 0; k < 12; k++) zz.c[k] = cmake<TS>(0, 0);
-      SPS::store(reinterpret_cast<char*>(src) + rhs * ss, n, g.N5, zz);
+      SPS::store_pair(reinterpret_cast<char*>(src) + rhs * ss, m, NP, zz, zz);
     }
   }
 }
@@ -360,17 +349,20 @@ __global__ void __launch_bounds__(kBlasThreads) sub64_norm_kernel(
   const int rhs = blockIdx.y;
   if (active && !active[rhs]) return;
   const size_t off = rhs * stride;
+  const int NP = g.N5 >> 1;
   double acc = 0.0;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
-    Spinor<double> x, y;
-    Store64::load(reinterpret_cast<const char*>(a) + off, n, g.N5, x);
-    Store64::load(reinterpret_cast<const char*>(b) + off, n, g.N5, y);
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < NP; m += gridDim.x * blockDim.x) {
+    Spinor<double> x[2], y[2];
+    Store64::load_pair(reinterpret_cast<const char*>(a) + off, m, NP, x[0], x[1]);
+    Store64::load_pair(reinterpret_cast<const char*>(b) + off, m, NP, y[0], y[1]);
 #pragma unroll
-    for (int k = 0; k < 12; k++) x.c[k] = x.c[k] - y.c[k];
-    Store64::store(reinterpret_cast<char*>(out) + off, n, g.N5, x);
-    acc += sqd(x);
+    for (int l = 0; l < 2; l++)
+#pragma unroll
+      for (int k = 0; k < 12; k++) x[l].c[k] = x[l].c[k] - y[l].c[k];
+    Store64::store_pair(reinterpret_cast<char*>(out) + off, m, NP, x[0], x[1]);
+    acc += sqd(x[0]) + sqd(x[1]);
   }
-  reduce_block(acc, red, rhs, gridDim.x, blockIdx.x);
+  block_sum_to(acc, red, rhs, gridDim.x, blockIdx.x);
 }
 
 template <class SP>
@@ -378,13 +370,34 @@ __global__ void __launch_bounds__(kBlasThreads) norm_kernel(const Geom g, const 
                                                              size_t stride, Reduce red) {
   using T = typename SP::T;
   const int rhs = blockIdx.y;
+  const int NP = g.N5 >> 1;
   double acc = 0.0;
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.N5; n += gridDim.x * blockDim.x) {
-    Spinor<T> a;
-    SP::load(reinterpret_cast<const char*>(x) + rhs * stride, n, g.N5, a);
-    acc += sqd(a);
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < NP; m += gridDim.x * blockDim.x) {
+    Spinor<T> a[2];
+    SP::load_pair(reinterpret_cast<const char*>(x) + rhs * stride, m, NP, a[0], a[1]);
+    acc += sqd(a[0]) + sqd(a[1]);
   }
-  reduce_block(acc, red, rhs, gridDim.x, blockIdx.x);
+  block_sum_to(acc, red, rhs, gridDim.x, blockIdx.x);
+}
+
+// Re <a, b> of two FP64 half-fields (one right-hand side per blockIdx.y).
+__global__ void __launch_bounds__(kBlasThreads) dot_re64_kernel(const Geom g, const void* a,
+                                                                 const void* b, size_t stride,
+                                                                 Reduce red) {
+  const int rhs = blockIdx.y;
+  const int NP = g.N5 >> 1;
+  double acc = 0.0;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < NP; m += gridDim.x * blockDim.x) {
+    Spinor<double> x[2], y[2];
+    Store64::load_pair(reinterpret_cast<const char*>(a) + rhs * stride, m, NP, x[0], x[1]);
+    Store64::load_pair(reinterpret_cast<const char*>(b) + rhs * stride, m, NP, y[0], y[1]);
+#pragma unroll
+    for (int l = 0; l < 2; l++)
+#pragma unroll
+      for (int k = 0; k < 12; k++)
+        acc = fma(x[l].c[k].re, y[l].c[k].re, fma(x[l].c[k].im, y[l].c[k].im, acc));
+  }
+  block_sum_to(acc, red, rhs, gridDim.x, blockIdx.x);
 }
 
 int elementwise_blocks(size_t n) {
@@ -396,7 +409,7 @@ int elementwise_blocks(size_t n) {
 
 }  // namespace
 
-int blas_grid_blocks(const Geom& g) { return elementwise_blocks((size_t)g.N5); }
+int blas_grid_blocks(const Geom& g) { return elementwise_blocks((size_t)g.N5 / 2); }
 
 size_t field_bytes(const Geom& g, int prec) {
   size_t b = 0;
@@ -479,7 +492,7 @@ cudaError_t launch_xr_update(const Geom& g, int prec, int xprec, void* x, void* 
                              const void* w, const double* num, const double* den, int sstride,
                              int nrhs, size_t stride_x, size_t stride, const Reduce* red,
                              cudaStream_t s, const int* active) {
-  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  dim3 grid(elementwise_blocks((size_t)g.N5 / 2), nrhs);
   if (xprec == prec) {
     DWF_PREC_SWITCH(prec, SP, xr_update_kernel<SP, SP><<<grid, kBlasThreads, 0, s>>>(g, x, r, p, w, num, den, sstride, stride_x, stride, *red, active));
   } else if (xprec == P32) {
@@ -493,7 +506,7 @@ cudaError_t launch_xr_update(const Geom& g, int prec, int xprec, void* x, void* 
 cudaError_t launch_p_update(const Geom& g, int prec, void* p, const void* z, const double* num,
                             const double* den, int sstride, int nrhs, size_t stride,
                             cudaStream_t s, const int* active) {
-  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  dim3 grid(elementwise_blocks((size_t)g.N5 / 2), nrhs);
   DWF_PREC_SWITCH(prec, SP, p_update_kernel<SP><<<grid, kBlasThreads, 0, s>>>(g, p, z, num, den, sstride, stride, active));
   return cudaGetLastError();
 }
@@ -501,7 +514,7 @@ cudaError_t launch_p_update(const Geom& g, int prec, void* p, const void* z, con
 template <class SPD>
 cudaError_t convert_from(const Geom& g, void* dst, int prec_s, const void* src, int nrhs, size_t sd,
                          size_t ss, const Reduce* red, cudaStream_t s, const int* active) {
-  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  dim3 grid(elementwise_blocks((size_t)g.N5 / 2), nrhs);
   Reduce r{};
   if (red) r = *red;
   const int dn = red != nullptr;
@@ -526,7 +539,7 @@ template <class SPX>
 cudaError_t px_from(const Geom& g, int prec, void* x, void* p, const void* z, const double* a_ptr,
                     const double* num, const double* den, int sstride, int nrhs, size_t sx,
                     size_t sp, cudaStream_t s, const int* active, int do_p) {
-  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  dim3 grid(elementwise_blocks((size_t)g.N5 / 2), nrhs);
   DWF_PREC_SWITCH(prec, SP, px_update_kernel<SPX, SP><<<grid, kBlasThreads, 0, s>>>(g, x, p, z, a_ptr, num, den, sstride, sx, sp, active, do_p));
   return cudaGetLastError();
 }
@@ -549,22 +562,29 @@ cudaError_t launch_x_update(const Geom& g, int prec, int xprec, void* x, const v
 
 cudaError_t launch_accumulate64(const Geom& g, void* x64, int prec_s, void* src, int zero_src,
                                 int nrhs, size_t sd, size_t ss, cudaStream_t s, const int* active) {
-  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  dim3 grid(elementwise_blocks((size_t)g.N5 / 2), nrhs);
   DWF_PREC_SWITCH(prec_s, SPS, accumulate64_kernel<SPS><<<grid, kBlasThreads, 0, s>>>(g, x64, src, zero_src, sd, ss, active));
   return cudaGetLastError();
 }
 
 cudaError_t launch_sub64_norm(const Geom& g, void* out, const void* a, const void* b, int nrhs,
                               size_t stride, const Reduce* red, cudaStream_t s, const int* active) {
-  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  dim3 grid(elementwise_blocks((size_t)g.N5 / 2), nrhs);
   sub64_norm_kernel<<<grid, kBlasThreads, 0, s>>>(g, out, a, b, stride, *red, active);
   return cudaGetLastError();
 }
 
 cudaError_t launch_norm(const Geom& g, int prec, const void* x, int nrhs, size_t stride,
                         const Reduce* red, cudaStream_t s) {
-  dim3 grid(elementwise_blocks((size_t)g.N5), nrhs);
+  dim3 grid(elementwise_blocks((size_t)g.N5 / 2), nrhs);
   DWF_PREC_SWITCH(prec, SP, norm_kernel<SP><<<grid, kBlasThreads, 0, s>>>(g, x, stride, *red));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot_re64(const Geom& g, const void* a, const void* b, int nrhs, size_t stride,
+                            const Reduce* red, cudaStream_t s) {
+  dim3 grid(elementwise_blocks((size_t)g.N5 / 2), nrhs);
+  dot_re64_kernel<<<grid, kBlasThreads, 0, s>>>(g, a, b, stride, *red);
   return cudaGetLastError();
 }
 

@@ -55,103 +55,128 @@ struct Link {
   cplx<T> u[9];  // row-major U[a][b] = u[3a+b]
 };
 
-// Position of slice s inside a 4D site's Ls consecutive 5D entries: even
-// slices first, then odd ones, so that threads owning the slice pairs
-// (2t, 2t+1) read and write contiguous memory for each of the two slices.
-__host__ __device__ __forceinline__ int slice_pos(int s, int Ls) {
-  return (s & 1) ? ((Ls + 1) >> 1) + (s >> 1) : (s >> 1);
-}
-__host__ __device__ __forceinline__ int site5(int h, int s, int Ls) { return h * Ls + slice_pos(s, Ls); }
+// 5D index of slice s of half-site h: n = h * Ls + s.  Slices are stored in
+// pairs: pair m = n >> 1 holds the slices 2j, 2j + 1 of one site (Ls even) in
+// its two lanes l = n & 1, so that a thread owning a slice pair reads both with
+// one vector load and computes on them with paired FP32 instructions.
+__host__ __device__ __forceinline__ int site5(int h, int s, int Ls) { return h * Ls + s; }
 
 // ---------------------------------------------------------------------------
-// Storage policies.  load/store one 5D site (index n) of one half-field.
+// Storage policies.  Half-field layout with NP = N5 / 2 slice pairs; for each
+// spinor component c = spin * 3 + colour, pair m stores
+// (re lane 0, re lane 1, im lane 0, im lane 1):
+//   FP64       double[12][NP][4]                                  192 B / site
+//   FP32       float [12][NP][4]                                   96 B / site
+//   FP16/BF16  uint4 [6][NP]: chunk j = components 2j, 2j+1 as the
+//              words (re c, im c, re c+1, im c+1), each word the 16-bit
+//              values of lane 0 (low half) and lane 1 (high half);
+//              then float scale[N5] (index n)                      52 B / site
+// load/store move one 5D site n (scalar lanes; the generic kernels and the
+// conversions); load_pair/store_pair move the two sites of pair m.
 // ---------------------------------------------------------------------------
 struct Store64 {
   using T = double;
   static constexpr int kPrec = P64;
-  static constexpr int kChunks = 12;     // 16-byte chunks per 5D site
   static constexpr bool kScaled = false;
+  __device__ static const double* at(const void* base, int c, int n, int N5) {
+    return reinterpret_cast<const double*>(base) + ((size_t)c * (N5 >> 1) + (n >> 1)) * 4 + (n & 1);
+  }
   __device__ static void load(const void* base, int n, int N5, Spinor<double>& o) {
-    const double2* b = reinterpret_cast<const double2*>(base);
 #pragma unroll
     for (int k = 0; k < 12; k++) {
-      double2 v = __ldg(b + (size_t)k * N5 + n);
-      o.c[k] = cmake(v.x, v.y);
+      const double* q = at(base, k, n, N5);
+      o.c[k] = cmake(__ldg(q), __ldg(q + 2));
     }
   }
   // spins of one chirality only (chir 0: spins 0,1; chir 1: spins 2,3)
   __device__ static void load_chir(const void* base, int n, int N5, int chir, Spinor<double>& o) {
-    const double2* b = reinterpret_cast<const double2*>(base);
 #pragma unroll
-    for (int k = 0; k < 6; k++) {
-      double2 v = __ldg(b + (size_t)(k + 6 * chir) * N5 + n);
-      o.c[k + 6 * chir] = cmake(v.x, v.y);
-    }
-  }
-  // the 6 complex components of one chirality into o[0..5]
-  __device__ static void load_half(const void* base, int n, int N5, int chir, cplx<double>* o) {
-    const double2* b = reinterpret_cast<const double2*>(base);
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-      double2 v = __ldg(b + (size_t)(k + 6 * chir) * N5 + n);
-      o[k] = cmake(v.x, v.y);
+    for (int k = 6 * chir; k < 6 * chir + 6; k++) {
+      const double* q = at(base, k, n, N5);
+      o.c[k] = cmake(__ldg(q), __ldg(q + 2));
     }
   }
   __device__ static void store(void* base, int n, int N5, const Spinor<double>& o) {
-    double2* b = reinterpret_cast<double2*>(base);
 #pragma unroll
-    for (int k = 0; k < 12; k++) b[(size_t)k * N5 + n] = make_double2(o.c[k].re, o.c[k].im);
+    for (int k = 0; k < 12; k++) {
+      double* q = const_cast<double*>(at(base, k, n, N5));
+      q[0] = o.c[k].re;
+      q[2] = o.c[k].im;
+    }
+  }
+  __device__ static void load_pair(const void* base, int m, int NP, Spinor<double>& a, Spinor<double>& b) {
+    const double2* p = reinterpret_cast<const double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const double2 re = __ldg(p + ((size_t)k * NP + m) * 2), im = __ldg(p + ((size_t)k * NP + m) * 2 + 1);
+      a.c[k] = cmake(re.x, im.x);
+      b.c[k] = cmake(re.y, im.y);
+    }
+  }
+  __device__ static void store_pair(void* base, int m, int NP, const Spinor<double>& a,
+                                    const Spinor<double>& b) {
+    double2* p = reinterpret_cast<double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      p[((size_t)k * NP + m) * 2] = make_double2(a.c[k].re, b.c[k].re);
+      p[((size_t)k * NP + m) * 2 + 1] = make_double2(a.c[k].im, b.c[k].im);
+    }
   }
 };
 
 struct Store32 {
   using T = float;
   static constexpr int kPrec = P32;
-  static constexpr int kChunks = 6;
   static constexpr bool kScaled = false;
+  __device__ static const float* at(const void* base, int c, int n, int N5) {
+    return reinterpret_cast<const float*>(base) + ((size_t)c * (N5 >> 1) + (n >> 1)) * 4 + (n & 1);
+  }
   __device__ static void load(const void* base, int n, int N5, Spinor<float>& o) {
-    const float4* b = reinterpret_cast<const float4*>(base);
 #pragma unroll
-    for (int k = 0; k < 6; k++) {
-      float4 v = __ldg(b + (size_t)k * N5 + n);
-      o.c[2 * k] = cmake(v.x, v.y);
-      o.c[2 * k + 1] = cmake(v.z, v.w);
+    for (int k = 0; k < 12; k++) {
+      const float* q = at(base, k, n, N5);
+      o.c[k] = cmake(__ldg(q), __ldg(q + 2));
     }
   }
   __device__ static void load_chir(const void* base, int n, int N5, int chir, Spinor<float>& o) {
-    const float4* b = reinterpret_cast<const float4*>(base);
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-      float4 v = __ldg(b + (size_t)(k + 3 * chir) * N5 + n);
-      o.c[2 * k + 6 * chir] = cmake(v.x, v.y);
-      o.c[2 * k + 1 + 6 * chir] = cmake(v.z, v.w);
-    }
-  }
-  __device__ static void load_half(const void* base, int n, int N5, int chir, cplx<float>* o) {
-    const float4* b = reinterpret_cast<const float4*>(base);
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      float4 v = __ldg(b + (size_t)(k + 3 * chir) * N5 + n);
-      o[2 * k] = cmake(v.x, v.y);
-      o[2 * k + 1] = cmake(v.z, v.w);
+    for (int k = 6 * chir; k < 6 * chir + 6; k++) {
+      const float* q = at(base, k, n, N5);
+      o.c[k] = cmake(__ldg(q), __ldg(q + 2));
     }
   }
   __device__ static void store(void* base, int n, int N5, const Spinor<float>& o) {
-    float4* b = reinterpret_cast<float4*>(base);
 #pragma unroll
-    for (int k = 0; k < 6; k++)
-      b[(size_t)k * N5 + n] = make_float4(o.c[2 * k].re, o.c[2 * k].im, o.c[2 * k + 1].re,
-                                          o.c[2 * k + 1].im);
+    for (int k = 0; k < 12; k++) {
+      float* q = const_cast<float*>(at(base, k, n, N5));
+      q[0] = o.c[k].re;
+      q[2] = o.c[k].im;
+    }
+  }
+  __device__ static void load_pair(const void* base, int m, int NP, Spinor<float>& a, Spinor<float>& b) {
+    const float4* p = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+      const float4 v = __ldg(p + (size_t)k * NP + m);
+      a.c[k] = cmake(v.x, v.z);
+      b.c[k] = cmake(v.y, v.w);
+    }
+  }
+  __device__ static void store_pair(void* base, int m, int NP, const Spinor<float>& a,
+                                    const Spinor<float>& b) {
+    float4* p = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; k++)
+      p[(size_t)k * NP + m] = make_float4(a.c[k].re, b.c[k].re, a.c[k].im, b.c[k].im);
   }
 };
 
-// 16-bit storage: 3 chunks of 8 values (uint4) per site, then one FP32 scale per
-// site after the 3 * N5 chunks.  value = stored * scale, scale = max |real|.
+// 16-bit storage with one FP32 scale per 5D site: value = stored * scale,
+// scale = max |real component| of the site.
 template <bool BF>
 struct Store16 {
   using T = float;
   static constexpr int kPrec = BF ? PB16 : P16;
-  static constexpr int kChunks = 3;
   static constexpr bool kScaled = true;
   __device__ static float to_f(uint16_t v) {
     if (BF) return __bfloat162float(__ushort_as_bfloat16(v));
@@ -161,75 +186,144 @@ struct Store16 {
     if (BF) return __bfloat16_as_ushort(__float2bfloat16_rn(f));
     return __half_as_ushort(__float2half_rn(f));
   }
+  // both lanes of a 32-bit word -> (lane 0, lane 1) as FP32
+  __device__ static float2 to_f2(uint32_t w) {
+    if (BF) return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+    return __half22float2(*reinterpret_cast<const __half2*>(&w));
+  }
+  // (lane 0, lane 1) -> one word, round to nearest
+  __device__ static uint32_t from_f2(float2 v) {
+    if (BF) {
+      const __nv_bfloat162 h = __float22bfloat162_rn(v);
+      return *reinterpret_cast<const uint32_t*>(&h);
+    }
+    const __half2 h = __float22half2_rn(v);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ static const float* scales(const void* base, int N5) {
+    return reinterpret_cast<const float*>(reinterpret_cast<const uint4*>(base) + (size_t)3 * N5);
+  }
+  // the 16-bit entries of component c of site n: re at [0], im at [2] (units of uint16)
+  __device__ static const uint16_t* at(const void* base, int c, int n, int N5) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint4*>(base) +
+                                                         (size_t)(c >> 1) * (N5 >> 1) + (n >> 1));
+    return reinterpret_cast<const uint16_t*>(w + 2 * (c & 1)) + (n & 1);
+  }
   __device__ static void load(const void* base, int n, int N5, Spinor<float>& o) {
-    const uint4* b = reinterpret_cast<const uint4*>(base);
-    const float sc = __ldg(reinterpret_cast<const float*>(b + (size_t)3 * N5) + n);
+    const float sc = __ldg(scales(base, N5) + n);
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-      uint4 v = __ldg(b + (size_t)k * N5 + n);
-      uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        o.c[4 * k + q] = cmake(sc * to_f((uint16_t)(w[q] & 0xffffu)), sc * to_f((uint16_t)(w[q] >> 16)));
-      }
+    for (int k = 0; k < 12; k++) {
+      const uint16_t* q = at(base, k, n, N5);
+      o.c[k] = cmake(sc * to_f(__ldg(q)), sc * to_f(__ldg(q + 2)));
     }
   }
   __device__ static void load_chir(const void* base, int n, int N5, int chir, Spinor<float>& o) {
     load(base, n, N5, o);
-  }
-  // chirality 0: complex 0..5 = chunk 0 (0..3) + low half of chunk 1 (4, 5);
-  // chirality 1: complex 6..11 = high half of chunk 1 (6, 7) + chunk 2 (8..11).
-  __device__ static void load_half(const void* base, int n, int N5, int chir, cplx<float>* o) {
-    const uint4* b = reinterpret_cast<const uint4*>(base);
-    const float sc = __ldg(reinterpret_cast<const float*>(b + (size_t)3 * N5) + n);
-    const uint4 v1 = __ldg(b + (size_t)N5 + n);
-    const uint4 v0 = __ldg(b + (size_t)(chir ? 2 : 0) * N5 + n);
-    uint32_t w[6];
-    if (chir == 0) {
-      w[0] = v0.x; w[1] = v0.y; w[2] = v0.z; w[3] = v0.w; w[4] = v1.x; w[5] = v1.y;
-    } else {
-      w[0] = v1.z; w[1] = v1.w; w[2] = v0.x; w[3] = v0.y; w[4] = v0.z; w[5] = v0.w;
-    }
-#pragma unroll
-    for (int q = 0; q < 6; q++)
-      o[q] = cmake(sc * to_f((uint16_t)(w[q] & 0xffffu)), sc * to_f((uint16_t)(w[q] >> 16)));
   }
   // Per-site scale from the largest |component|.  Below the smallest normal float
   // (subnormal or zero, e.g. the far tail of a point-source solve) 1/max would
   // overflow to inf: such a site keeps scale 1, and its components, far below
   // 16-bit resolution, store as zero.  A NaN component still stores as NaN.
   __device__ static float scale_of(float mx) { return mx >= 1.17549435e-38f ? mx : 1.f; }
-  // o <- what store() followed by load() gives back, computed in registers (a
-  // kernel must not re-read through __ldg what it wrote itself).
-  __device__ static void quantize(Spinor<float>& o) {
+  __device__ static float maxabs(const Spinor<float>& o) {
     float mx = 0.f;
 #pragma unroll
     for (int k = 0; k < 12; k++) mx = fmaxf(mx, fmaxf(fabsf(o.c[k].re), fabsf(o.c[k].im)));
-    const float sc = scale_of(mx);
+    return mx;
+  }
+  // o <- what store() followed by load() gives back, computed in registers (a
+  // kernel must not re-read through __ldg what it wrote itself).
+  __device__ static void quantize(Spinor<float>& o) {
+    const float sc = scale_of(maxabs(o));
     const float inv = 1.f / sc;
 #pragma unroll
     for (int k = 0; k < 12; k++)
       o.c[k] = cmake(sc * to_f(from_f(o.c[k].re * inv)), sc * to_f(from_f(o.c[k].im * inv)));
   }
+  // One site: 16-bit stores of its own lane only (the other lane of each word
+  // belongs to the neighbouring slice, possibly written by another thread).
   __device__ static void store(void* base, int n, int N5, const Spinor<float>& o) {
-    uint4* b = reinterpret_cast<uint4*>(base);
-    float mx = 0.f;
-#pragma unroll
-    for (int k = 0; k < 12; k++) mx = fmaxf(mx, fmaxf(fabsf(o.c[k].re), fabsf(o.c[k].im)));
-    const float sc = scale_of(mx);
+    const float sc = scale_of(maxabs(o));
     const float inv = 1.f / sc;
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-      uint32_t w[4];
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        w[q] = (uint32_t)from_f(o.c[4 * k + q].re * inv) | ((uint32_t)from_f(o.c[4 * k + q].im * inv) << 16);
-      }
-      b[(size_t)k * N5 + n] = make_uint4(w[0], w[1], w[2], w[3]);
+    for (int k = 0; k < 12; k++) {
+      uint16_t* q = const_cast<uint16_t*>(at(base, k, n, N5));
+      q[0] = from_f(o.c[k].re * inv);
+      q[2] = from_f(o.c[k].im * inv);
     }
-    reinterpret_cast<float*>(b + (size_t)3 * N5)[n] = sc;
+    const_cast<float*>(scales(base, N5))[n] = sc;
+  }
+  __device__ static void load_pair(const void* base, int m, int NP, Spinor<float>& a, Spinor<float>& b) {
+    const uint4* p = reinterpret_cast<const uint4*>(base);
+    const float2 sc = __ldg(reinterpret_cast<const float2*>(p + (size_t)6 * NP) + m);
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+      const uint4 v = __ldg(p + (size_t)j * NP + m);
+      const float2 r0 = to_f2(v.x), i0 = to_f2(v.y), r1 = to_f2(v.z), i1 = to_f2(v.w);
+      a.c[2 * j] = cmake(sc.x * r0.x, sc.x * i0.x);
+      b.c[2 * j] = cmake(sc.y * r0.y, sc.y * i0.y);
+      a.c[2 * j + 1] = cmake(sc.x * r1.x, sc.x * i1.x);
+      b.c[2 * j + 1] = cmake(sc.y * r1.y, sc.y * i1.y);
+    }
+  }
+  __device__ static void store_pair(void* base, int m, int NP, const Spinor<float>& a,
+                                    const Spinor<float>& b) {
+    uint4* p = reinterpret_cast<uint4*>(base);
+    const float sa = scale_of(maxabs(a)), sb = scale_of(maxabs(b));
+    const float ia = 1.f / sa, ib = 1.f / sb;
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+      const int c0 = 2 * j, c1 = 2 * j + 1;
+      p[(size_t)j * NP + m] =
+          make_uint4(from_f2(make_float2(a.c[c0].re * ia, b.c[c0].re * ib)),
+                     from_f2(make_float2(a.c[c0].im * ia, b.c[c0].im * ib)),
+                     from_f2(make_float2(a.c[c1].re * ia, b.c[c1].re * ib)),
+                     from_f2(make_float2(a.c[c1].im * ia, b.c[c1].im * ib)));
+    }
+    reinterpret_cast<float2*>(p + (size_t)6 * NP)[m] = make_float2(sa, sb);
   }
 };
+
+// ---------------------------------------------------------------------------
+// Deterministic two-level sum of one double per thread into red.result[rhs]:
+// warp shuffles, one partial per block (block bid of nblocks), and the last
+// block of the right-hand side to finish (ticket from red.counter) adds the
+// partials in block order.  Every thread of the block must call it (it
+// synchronises the block); works for 1D and 2D blocks.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_sum_to(double v, const Reduce& red, int rhs, int nblocks,
+                                             int bid) {
+  __shared__ double wsum[32];
+  const int nth = blockDim.x * blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (nth + 31) >> 5;
+    v = lane < nw ? wsum[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    double* part = red.partial + (size_t)rhs * red.partial_stride;
+    unsigned int ticket = 0;
+    if (lane == 0) {
+      part[bid] = v;
+      __threadfence();
+      ticket = atomicAdd(red.counter + rhs, 1u);
+    }
+    ticket = __shfl_sync(0xffffffffu, ticket, 0);
+    if (ticket == (unsigned)(nblocks - 1)) {
+      __threadfence();
+      double acc = 0.0;
+      for (int b = lane; b < nblocks; b += 32) acc += *((volatile double*)(part + b));
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+      if (lane == 0) {
+        red.result[(size_t)rhs * red.result_stride] = acc;
+        red.counter[rhs] = 0u;
+      }
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Gauge policies: link of a half-site h in direction mu.

@@ -14,41 +14,6 @@ namespace {
 
 constexpr int kSitePad = 4;  // shared-memory padding per 4D site (bank spread)
 
-// Deterministic two-level reduction: warp shuffles, one partial per block, the
-// last block of a right-hand side sums the partials in block order.
-__device__ void block_reduce_finish(double v, const Reduce& red, int rhs, int nblocks, int bid) {
-  __shared__ double wsum[32];
-  const int nth = blockDim.x * blockDim.y;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if (lane == 0) wsum[warp] = v;
-  __syncthreads();
-  if (warp == 0) {
-    const int nw = (nth + 31) >> 5;
-    v = lane < nw ? wsum[lane] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    double* part = red.partial + (size_t)rhs * red.partial_stride;
-    unsigned int ticket = 0;
-    if (lane == 0) {
-      part[bid] = v;
-      __threadfence();
-      ticket = atomicAdd(red.counter + rhs, 1u);
-    }
-    ticket = __shfl_sync(0xffffffffu, ticket, 0);
-    if (ticket == (unsigned)(nblocks - 1)) {
-      __threadfence();
-      double acc = 0.0;
-      for (int b = lane; b < nblocks; b += 32) acc += *((volatile double*)(part + b));
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-      if (lane == 0) {
-        red.result[(size_t)rhs * red.result_stride] = acc;
-        red.counter[rhs] = 0u;
-      }
-    }
-  }
-}
-
 template <typename T>
 __device__ __forceinline__ T sq(const Spinor<T>& a) {
   T r = 0;
@@ -250,7 +215,7 @@ __global__ void __launch_bounds__(256) hop_kernel(const Geom g, const HopArgs<ty
   if (active) SP::store(reinterpret_cast<char*>(a.out) + off, site5(h, s, Ls), g.N5, res);
   if (NORM) {
     double v = active ? (double)sq(res) : 0.0;
-    block_reduce_finish(v, a.red, rhs, gridDim.x, blockIdx.x);
+    block_sum_to(v, a.red, rhs, gridDim.x, blockIdx.x);
   }
 }
 
@@ -293,7 +258,7 @@ __global__ void __launch_bounds__(256) local_kernel(const Geom g, void* out, con
   if (active) SP::store(reinterpret_cast<char*>(out) + off, site5(h, s, Ls), g.N5, res);
   if (do_norm) {
     double v = active ? (double)sq(res) : 0.0;
-    block_reduce_finish(v, red, rhs, gridDim.x, blockIdx.x);
+    block_sum_to(v, red, rhs, gridDim.x, blockIdx.x);
   }
 }
 

@@ -1,14 +1,13 @@
 // dwf_internal.cuh -- layouts, geometry and kernel launchers shared by the
 // translation units of libdwf (GB300, sm_103a).
 //
-// Internal half-field layout (5th dimension innermost):
-//   5D index n = h * Ls + slice_pos(s), h the half-lattice site index of the
-//   canonical layout, slice_pos placing the even slices of a site before the
-//   odd ones (dwf_fields.cuh); N5 = Vh * Ls.  Components are stored chunk-major so that a warp
-//   reading one chunk of 32 consecutive n touches 512 contiguous bytes:
-//     FP64  double2 [12][N5]   (one complex per chunk, spin-major: spin*3+colour)
-//     FP32  float4  [6][N5]    (two complex per chunk)
-//     FP16/BF16  uint4 [3][N5] (four complex per chunk) + float scale[N5]
+// Internal half-field layout (5th dimension innermost): 5D index n = h * Ls + s,
+// h the half-lattice site index of the canonical layout; N5 = Vh * Ls.  The
+// slices are stored in pairs (pair m = n >> 1, lane n & 1; dwf_fields.cuh), each
+// spinor component of a pair as (re lane 0, re lane 1, im lane 0, im lane 1):
+//     FP64  double[12][N5/2][4]
+//     FP32  float [12][N5/2][4]
+//     FP16/BF16  uint4[6][N5/2] (two components per chunk) + float scale[N5]
 //   Spins 0, 1 are the P_+ chirality (gamma5 = +1), spins 2, 3 are P_-.
 //
 // Gauge layout per parity p (sites of parity p, half index h):
@@ -204,6 +203,9 @@ cudaError_t launch_sub64_norm(const Geom& g, void* out, const void* a, const voi
 // |x|^2 -> red.
 cudaError_t launch_norm(const Geom& g, int prec, const void* x, int nrhs, size_t stride,
                         const Reduce* red, cudaStream_t s);
+// Re <a, b> of FP64 half-fields -> red.
+cudaError_t launch_dot_re64(const Geom& g, const void* a, const void* b, int nrhs, size_t stride,
+                            const Reduce* red, cudaStream_t s);
 // Number of blocks the BLAS-1 launches use (partial buffers must hold this many).
 int blas_grid_blocks(const Geom& g);
 

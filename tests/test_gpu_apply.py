@@ -140,26 +140,6 @@ def test_tuned_matches_generic(Ls, prec, monkeypatch):
         assert site_norm_error(outs[0][k], outs[1][k]) <= tol
 
 
-@pytest.mark.parametrize("Ls", [8, 12, 16])
-@pytest.mark.parametrize("prec", [1, 2, 3])
-def test_staged_matches_direct_loads(Ls, prec, monkeypatch):
-    """Bulk-copy staged neighbours (DWF_TMA=1) against direct loads: bitwise equal."""
-    sysm = make_case((4, 4, 2, 6), Ls, "varying", alpha=0.8, bc_t=-1, black=1)
-    psi = gaussian_half5d(sysm.lattice, Ls, seed=9)
-    outs = []
-    for staged in (False, True):
-        if staged:
-            monkeypatch.setenv("DWF_TMA", "1")
-        else:
-            monkeypatch.delenv("DWF_TMA", raising=False)
-        op = _op(sysm)
-        outs.append((_apply(op, psi, prec), _apply(op, psi, prec, dag=True)))
-        op.close()
-    monkeypatch.delenv("DWF_TMA", raising=False)
-    for k in range(2):
-        assert np.array_equal(outs[0][k], outs[1][k])
-
-
 @pytest.mark.parametrize("L,prec,tol", [((16, 16, 16, 32), 1, 5e-6), ((16, 16, 16, 32), 0, 1e-12),
                                          ((32, 32, 32, 64), 1, 5e-6)])
 def test_full_size_sampled_parity(L, prec, tol):
