@@ -203,8 +203,12 @@ struct dwf_ctx {
   void* gauge[3] = {nullptr, nullptr, nullptr};  // FP64, FP32, FP16
   int* nbr = nullptr;                            // [2][Vh][8] neighbour table
   int* dev_err = nullptr;                        // set by a kernel whose bounded wait gave up
-  int use_tma = 0;                               // DWF_TMA: bulk-copy staged tuned kernels
+  int use_tma = 0;                               // DWF_TMA: tensor-copy staged tuned kernels
+  long long wait_budget = 0;                     // DWF_WAIT_BUDGET: clock cycles per bounded wait
+  int skip_hop = -1;                             // DWF_TEST_SKIP_HOP: staged kernels issue no
+                                                 // copies for this hop (timeout test hook)
   bool fused_cg = true;                          // DWF_UNFUSED_CG unset: fused CG BLAS steps
+  bool bp_fused = true;                          // DWF_NO_BP_FUSED unset: p update forms B p
   int check = 16;                                // effective iterations between polls
   bool gauge_loaded = false;
   std::vector<void*> allocs;
@@ -401,6 +405,8 @@ HopLaunch base_hop(dwf_ctx* h, int prec, int p, int nrhs, size_t stride) {
   L.nbr = h->nbr;
   L.err = h->dev_err;
   L.use_tma = h->use_tma;
+  L.wait_budget = h->wait_budget;
+  L.skip_hop = h->skip_hop;
   return L;
 }
 
@@ -445,6 +451,37 @@ int apply_dbb(dwf_ctx* h, const CoefView& cv, int prec, void* out, const void* i
   B.out = out;
   B.v = tmp;
   B.w = in;
+  B.post = cv.ptr(prec, ms.mat_off(MatSet::IINV));
+  B.post_prog = hop2::PR_IINV;
+  B.chain = cv.ptr(prec, ms.chain_off());
+  B.loc = LOC_ID;
+  B.c_hop = -0.25;
+  B.c_loc = 1.0;
+  B.red = norm;
+  set_coef(B, cv);
+  KLAUNCH(h, launch_hop(h->g, B, s));
+  return DWF_OK;
+}
+
+// out = D_bb p given bp = B p (the fused CG forms B p with p): pass A hops bp
+// without the B pre-multiplication, pass B as in apply_dbb.
+int apply_dbb_bp(dwf_ctx* h, const CoefView& cv, int prec, void* out, const void* p, const void* bp,
+                 void* tmp, int nrhs, const Reduce* norm, cudaStream_t s) {
+  const MatSet& ms = *cv.layout;
+  const int black = h->opt.rb_parity, red = 1 - black;
+  const size_t st = field_bytes(h->g, prec);
+  HopLaunch A = base_hop(h, prec, red, nrhs, st);
+  A.out = tmp;
+  A.v = bp;
+  A.post = cv.ptr(prec, ms.mat_off(MatSet::K));
+  A.post_prog = hop2::PR_K;
+  A.chain = cv.ptr(prec, ms.chain_off());
+  set_coef(A, cv);
+  KLAUNCH(h, launch_hop(h->g, A, s));
+  HopLaunch B = base_hop(h, prec, black, nrhs, st);
+  B.out = out;
+  B.v = tmp;
+  B.w = p;
   B.post = cv.ptr(prec, ms.mat_off(MatSet::IINV));
   B.post_prog = hop2::PR_IINV;
   B.chain = cv.ptr(prec, ms.chain_off());
@@ -583,6 +620,7 @@ bool is_device_ptr(const void* p) {
 struct SolveWork {
   void *b_hi, *x_hi, *r_hi, *t64, *t64r;  // FP64 black (t64r red)
   void *p, *r, *w, *z, *xlo, *tb, *tr;    // inner precision
+  void *p2, *bp;                          // second p buffer and B p (fused CG, FP32/FP64)
 };
 
 int alloc_solve_work(dwf_ctx* h, int prec, SolveWork& W, int nb = 1) {
@@ -602,13 +640,19 @@ int alloc_solve_work(dwf_ctx* h, int prec, SolveWork& W, int nb = 1) {
   if ((rc = get_ws(h, "xlo" + sfx, field_bytes(h->g, xprec) * nb, &W.xlo))) return rc;
   if ((rc = get_ws(h, "tb" + sfx, fi, &W.tb))) return rc;
   if ((rc = get_ws(h, "tr" + sfx, fi, &W.tr))) return rc;
+  W.p2 = W.bp = nullptr;
+  if (prec == P32 || prec == P64) {
+    if ((rc = get_ws(h, "p2" + sfx, fi, &W.p2))) return rc;
+    if ((rc = get_ws(h, "bp" + sfx, fi, &W.bp))) return rc;
+  }
   return DWF_OK;
 }
 
 // Bytes of solver workspace per right-hand side (used by the autotuner's memory check).
 size_t solve_bytes_per_rhs(const Geom& g, int prec) {
   const int xprec = (prec == P16 || prec == PB16) ? P32 : prec;
-  return 5 * field_bytes(g, P64) + 6 * field_bytes(g, prec) + field_bytes(g, xprec);
+  const int extra = (prec == P32 || prec == P64) ? 2 : 0;  // second p buffer, B p
+  return 5 * field_bytes(g, P64) + (6 + extra) * field_bytes(g, prec) + field_bytes(g, xprec);
 }
 
 // Start/stop events around one apply (kind 0: D_bb, 1: D_bb^+) when profiling.
@@ -758,6 +802,9 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
   const bool fused = form == DWF_SCHUR_PRECOND && h->fused_cg && !g_disable_tuned &&
                      (Ls == 8 || Ls == 12 || Ls == 16);
   if (fused && (rc = apply_hat(h, cv, prec, W.tb, W.r, nb, s))) return rc;
+  // FP32 / FP64 inner fields: the p update also forms B p for D_bb pass A
+  const bool with_bp = fused && W.bp != nullptr && h->bp_fused;
+  if (with_bp) CUCHK(h, cudaMemsetAsync(W.p2, 0, fi * nb, s));
 
   auto enqueue_fused = [&](int cur, bool first) -> int {
     const int nxt = 1 - cur;
@@ -767,13 +814,29 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
     if ((r = timer_mark(h, s, true, 1))) return r;
     if ((r = apply_dbb_dag_hat(h, cv, prec, W.z, W.r, W.tb, W.tr, nb, &red_zz[nxt], s))) return r;
     if ((r = timer_mark(h, s, false, 1))) return r;
-    if (first)
+    void* pcur = W.p;
+    if (with_bp) {
+      // p_new = z + beta p and B p_new into the other p buffer (even/odd iterations
+      // alternate, so after the even number of iterations between polls W.p is current)
+      void* pold = cur ? W.p2 : W.p;
+      pcur = cur ? W.p : W.p2;
+      KLAUNCH(h, launch_pxb_update(h->g, prec, xprec, W.xlo, pold, pcur, W.bp, W.z, h->scal + S_A,
+                                   zz_new, zz_old, kScal, nb, fx, fi,
+                                   cv.ptr(prec, cv.layout->bdiag_off()),
+                                   cv.ptr(prec, cv.layout->boff_off()), cv.cstride, s, h->d_active,
+                                   first ? 0 : 1));
+    } else if (first) {
       KLAUNCH(h, launch_p_update(h->g, prec, W.p, W.z, zz_new, zz_old, kScal, nb, fi, s, h->d_active));
-    else
+    } else {
       KLAUNCH(h, launch_px_update(h->g, prec, xprec, W.xlo, W.p, W.z, h->scal + S_A, zz_new, zz_old,
                                   kScal, nb, fx, fi, s, h->d_active));
+    }
     if ((r = timer_mark(h, s, true, 0))) return r;
-    if ((r = apply_dbb(h, cv, prec, W.w, W.p, W.tr, nb, &red_ww, s))) return r;
+    if (with_bp) {
+      if ((r = apply_dbb_bp(h, cv, prec, W.w, pcur, W.bp, W.tr, nb, &red_ww, s))) return r;
+    } else if ((r = apply_dbb(h, cv, prec, W.w, W.p, W.tr, nb, &red_ww, s))) {
+      return r;
+    }
     if ((r = timer_mark(h, s, false, 0))) return r;
     RUpdateLaunch U{};
     U.prec = prec;
@@ -1178,7 +1241,7 @@ int choose_rhs_block(dwf_ctx* h, int nrhs, int prec, cudaStream_t st, int* nb_ou
   double best = 1e300;
   int best_nb = 1, best_tma = saved_tma;
   for (int nb : ok) {
-    for (int tma = 0; tma < 1; tma++) {
+    for (int tma = 0; tma < 2; tma++) {
       h->use_tma = tma;
       if ((rc = apply_dbb(h, view_of(*ms), prec, y, x, t, nb, nullptr, st))) return rc;
       CUCHK(h, cudaEventRecord(e0, st));
@@ -1274,6 +1337,9 @@ int dwf_create(dwf_handle* out, const int lattice[4], int Ls, double M5, double 
   // through shared memory with cp.async.bulk (measured slower than direct
   // loads on the 16^3x32 workload; kept as an alternative staging strategy).
   h->use_tma = std::getenv("DWF_TMA") != nullptr;
+  h->bp_fused = std::getenv("DWF_NO_BP_FUSED") == nullptr;
+  if (const char* e = std::getenv("DWF_WAIT_BUDGET")) h->wait_budget = std::atoll(e);
+  if (const char* e = std::getenv("DWF_TEST_SKIP_HOP")) h->skip_hop = std::atoi(e);
   h->fused_cg = std::getenv("DWF_UNFUSED_CG") == nullptr;
   cudaGetDevice(&h->device);
   if (cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess) {

@@ -287,6 +287,85 @@ __global__ void __launch_bounds__(kBlasThreads) px_update_kernel(
   }
 }
 
+// p_new = z + beta p_old (and, with do_x, the deferred x += a_prev p_old) for one
+// slice pair m of site h, t = m mod (Ls/2), plus bp = B p_new: B is cyclic
+// bidiagonal per chirality (Eq. mobius1 with D_w -> 1),
+//   (B v)+(s) = d+(s) v+(s) + o+(s) v+(s-1),  (B v)-(s) = d-(s) v-(s) + o-(s) v-(s+1),
+// so v+ of slice 2t-1 (pair below) and v- of slice 2t+2 (pair above) are formed
+// from z and p of those pairs as well.  Used by the CG on the tuned path, whose
+// D_bb pass A then hops B p directly.  p_old and p_new are different buffers
+// (neighbouring pairs of p_old are read while p_new is written).
+template <class SPX, class SP>
+__global__ void __launch_bounds__(kBlasThreads) pxb_update_kernel(
+    const Geom g, void* x, const void* p, void* pnew, void* bp, const void* z, const double* a_ptr,
+    const double* num, const double* den, int sstride, size_t stride_x, size_t stride,
+    const typename SP::T* bdiag, const typename SP::T* boff, size_t cstride, const int* active,
+    int do_x) {
+  using T = typename SP::T;
+  using TX = typename SPX::T;
+  const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
+  const size_t off = rhs * stride, offx = rhs * stride_x;
+  const TX a = do_x ? (TX)a_ptr[(size_t)rhs * sstride] : (TX)0;
+  const T beta = (T)(num[(size_t)rhs * sstride] / den[(size_t)rhs * sstride]);
+  const int NP = g.N5 >> 1, half = g.Ls >> 1;
+  const T* bd = bdiag + (size_t)rhs * cstride;
+  const T* bo = boff + (size_t)rhs * cstride;
+  const char* pb = reinterpret_cast<const char*>(p) + off;
+  const char* zb = reinterpret_cast<const char*>(z) + off;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < NP; m += gridDim.x * blockDim.x) {
+    const int t = m % half, base = m - t;
+    const int mp = base + (t == 0 ? half - 1 : t - 1), mn = base + (t + 1 == half ? 0 : t + 1);
+    Spinor<T> pv[2], zv[2], pl[2], zl[2], pu[2], zu[2];
+    SP::load_pair(pb, m, NP, pv[0], pv[1]);
+    SP::load_pair(zb, m, NP, zv[0], zv[1]);
+    SP::load_pair(pb, mp, NP, pl[0], pl[1]);
+    SP::load_pair(zb, mp, NP, zl[0], zl[1]);
+    SP::load_pair(pb, mn, NP, pu[0], pu[1]);
+    SP::load_pair(zb, mn, NP, zu[0], zu[1]);
+    if (do_x) {
+      Spinor<TX> xv[2];
+      SPX::load_pair(reinterpret_cast<const char*>(x) + offx, m, NP, xv[0], xv[1]);
+#pragma unroll
+      for (int l = 0; l < 2; l++)
+#pragma unroll
+        for (int k = 0; k < 12; k++)
+          xv[l].c[k] = cmake(fma(a, (TX)pv[l].c[k].re, xv[l].c[k].re), fma(a, (TX)pv[l].c[k].im, xv[l].c[k].im));
+      SPX::store_pair(reinterpret_cast<char*>(x) + offx, m, NP, xv[0], xv[1]);
+    }
+    // p_new on the pair, v+ of the slice below and v- of the slice above
+    Spinor<T> q[2];
+    cplx<T> below[6], above[6];
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+#pragma unroll
+      for (int l = 0; l < 2; l++)
+        q[l].c[k] = cmake(fma(beta, pv[l].c[k].re, zv[l].c[k].re), fma(beta, pv[l].c[k].im, zv[l].c[k].im));
+    }
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      below[k] = cmake(fma(beta, pl[1].c[k].re, zl[1].c[k].re), fma(beta, pl[1].c[k].im, zl[1].c[k].im));
+      above[k] = cmake(fma(beta, pu[0].c[6 + k].re, zu[0].c[6 + k].re),
+                       fma(beta, pu[0].c[6 + k].im, zu[0].c[6 + k].im));
+    }
+    SP::store_pair(reinterpret_cast<char*>(pnew) + off, m, NP, q[0], q[1]);
+    const int s0 = 2 * t;
+    const T dp0 = bd[s0], dp1 = bd[s0 + 1], op0 = bo[s0], op1 = bo[s0 + 1];
+    const T dm0 = bd[g.Ls + s0], dm1 = bd[g.Ls + s0 + 1], om0 = bo[g.Ls + s0], om1 = bo[g.Ls + s0 + 1];
+    Spinor<T> b[2];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      b[0].c[k] = cmake(fma(op0, below[k].re, dp0 * q[0].c[k].re), fma(op0, below[k].im, dp0 * q[0].c[k].im));
+      b[1].c[k] = cmake(fma(op1, q[0].c[k].re, dp1 * q[1].c[k].re), fma(op1, q[0].c[k].im, dp1 * q[1].c[k].im));
+      b[0].c[6 + k] = cmake(fma(om0, q[1].c[6 + k].re, dm0 * q[0].c[6 + k].re),
+                            fma(om0, q[1].c[6 + k].im, dm0 * q[0].c[6 + k].im));
+      b[1].c[6 + k] = cmake(fma(om1, above[k].re, dm1 * q[1].c[6 + k].re),
+                            fma(om1, above[k].im, dm1 * q[1].c[6 + k].im));
+    }
+    SP::store_pair(reinterpret_cast<char*>(bp) + off, m, NP, b[0], b[1]);
+  }
+}
+
 // dst <- src converted; the norm (optional) is that of the stored dst values.
 template <class SPD, class SPS>
 __global__ void __launch_bounds__(kBlasThreads) convert_kernel(
@@ -558,6 +637,30 @@ cudaError_t launch_x_update(const Geom& g, int prec, int xprec, void* x, const v
   void* pp = const_cast<void*>(p);
   if (xprec == P64) return px_from<Store64>(g, prec, x, pp, nullptr, a_ptr, a_ptr, a_ptr, sstride, nrhs, sx, sp, s, active, 0);
   return px_from<Store32>(g, prec, x, pp, nullptr, a_ptr, a_ptr, a_ptr, sstride, nrhs, sx, sp, s, active, 0);
+}
+
+cudaError_t launch_pxb_update(const Geom& g, int prec, int xprec, void* x, const void* p,
+                              void* pnew, void* bp, const void* z, const double* a_ptr, const double* num,
+                              const double* den, int sstride, int nrhs, size_t sx, size_t sp,
+                              const void* bdiag, const void* boff, size_t cstride, cudaStream_t s,
+                              const int* active, int do_x) {
+  dim3 grid(elementwise_blocks((size_t)g.N5 / 2), nrhs);
+  if (prec == P32 && xprec == P32) {
+    pxb_update_kernel<Store32, Store32><<<grid, kBlasThreads, 0, s>>>(
+        g, x, p, pnew, bp, z, a_ptr, num, den, sstride, sx, sp, reinterpret_cast<const float*>(bdiag),
+        reinterpret_cast<const float*>(boff), cstride, active, do_x);
+  } else if (prec == P32 && xprec == P64) {
+    pxb_update_kernel<Store64, Store32><<<grid, kBlasThreads, 0, s>>>(
+        g, x, p, pnew, bp, z, a_ptr, num, den, sstride, sx, sp, reinterpret_cast<const float*>(bdiag),
+        reinterpret_cast<const float*>(boff), cstride, active, do_x);
+  } else if (prec == P64 && xprec == P64) {
+    pxb_update_kernel<Store64, Store64><<<grid, kBlasThreads, 0, s>>>(
+        g, x, p, pnew, bp, z, a_ptr, num, den, sstride, sx, sp, reinterpret_cast<const double*>(bdiag),
+        reinterpret_cast<const double*>(boff), cstride, active, do_x);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_accumulate64(const Geom& g, void* x64, int prec_s, void* src, int zero_src,

@@ -25,6 +25,8 @@
 
 #include <cstdlib>
 
+#include <cudaTypedefs.h>
+
 #include "dwf_fields.cuh"
 
 namespace dwf {
@@ -268,7 +270,105 @@ struct Args {
   Reduce red;
   size_t cstride;       // elements between right-hand sides of bdiag, boff, chain
   const int* active;    // per right-hand side: 0 skips it (nullptr: all active)
+  int* err;             // set to 1 when a bounded wait gives up (staged variant)
 };
+
+// h = P_+ - dir A P_- (in place into P), chi_k = U' h_k, acc_upper(k) += f chi_k,
+// acc_lower(pk) += f rs (i) chi_k; U' = U (dir > 0) or U^+ (dir < 0).
+template <class SP, int MU, int DIR>
+__device__ __forceinline__ void project_mul_acc(HalfP<typename Pr<typename SP::T>::V>& P,
+                                                const HalfP<typename Pr<typename SP::T>::V>& M,
+                                                const Link<typename SP::T>& U,
+                                                typename Pr<typename SP::T>::V f,
+                                                SpinP<typename Pr<typename SP::T>::V>& acc) {
+  using T = typename SP::T;
+  using A = Pr<T>;
+  using V = typename A::V;
+  // projection h = P_+ - dir A P_- (in place into P)
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const int pk = partner(MU, k);
+    const int cs = proj_sign(MU, DIR, k);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const V pr = P.re[3 * k + a], pi = P.im[3 * k + a];
+      const V mr = M.re[3 * pk + a], mi = M.im[3 * pk + a];
+      if (imag_mu(MU)) {  // P + cs i M
+        P.re[3 * k + a] = cs > 0 ? A::sub(pr, mi) : A::add(pr, mi);
+        P.im[3 * k + a] = cs > 0 ? A::add(pi, mr) : A::sub(pi, mr);
+      } else {            // P + cs M
+        P.re[3 * k + a] = cs > 0 ? A::add(pr, mr) : A::sub(pr, mr);
+        P.im[3 * k + a] = cs > 0 ? A::add(pi, mi) : A::sub(pi, mi);
+      }
+    }
+  }
+  const V fn = A::neg(f);
+  // chi_k = U' h_k; acc_upper(k) += f chi_k; acc_lower(pk) += f rs (i) chi_k
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const int q = partner(MU, k);  // lower row fed by chi_k
+    const int rs = recon_sign(MU, DIR, q);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      V cr, ci;
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        const cplx<T> u = DIR > 0 ? U.u[3 * a + b] : U.u[3 * b + a];
+        const V ur = A::dup(u.re);
+        const V ui = A::dup(DIR > 0 ? u.im : -u.im);
+        const V hr = P.re[3 * k + b], hi = P.im[3 * k + b];
+        if (b == 0) {
+          cr = A::mul(ur, hr);
+          ci = A::mul(ur, hi);
+        } else {
+          cr = A::fma(ur, hr, cr);
+          ci = A::fma(ur, hi, ci);
+        }
+        cr = A::fma(A::neg(ui), hi, cr);
+        ci = A::fma(ui, hr, ci);
+      }
+      acc.re[3 * k + a] = A::fma(f, cr, acc.re[3 * k + a]);
+      acc.im[3 * k + a] = A::fma(f, ci, acc.im[3 * k + a]);
+      const int l = 6 + 3 * q + a;
+      if (imag_mu(MU)) {  // += rs i chi: re -= rs chi_im, im += rs chi_re
+        acc.re[l] = A::fma(rs > 0 ? fn : f, ci, acc.re[l]);
+        acc.im[l] = A::fma(rs > 0 ? f : fn, cr, acc.im[l]);
+      } else {            // += rs chi
+        acc.re[l] = A::fma(rs > 0 ? f : fn, cr, acc.re[l]);
+        acc.im[l] = A::fma(rs > 0 ? f : fn, ci, acc.im[l]);
+      }
+    }
+  }
+}
+
+// L2 prefetch of the neighbour data of one hop: the site's slice-pair block of
+// every spinor component (one 128-byte line per component at Ls = 16), spread
+// over the Ls/2 threads of the site, and the link of a backward hop.  Issued a
+// few hops ahead so that first touches of DRAM overlap the current hop.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+template <class SP, int LS, int DIR>
+__device__ __forceinline__ void prefetch_hop(int nb, int t, size_t NP, const void* v, const void* gq,
+                                             int mu) {
+  constexpr int HALF = LS / 2;
+  constexpr int kComp = SP::kPrec == P64 ? 24 : (SP::kScaled ? 6 : 12);  // 16-byte chunk rows
+  const int hn = nb & 0x7fffffff;
+  const size_t m0 = (size_t)hn * HALF;
+  const char* b = reinterpret_cast<const char*>(v);
+#pragma unroll
+  for (int c = t; c < kComp; c += HALF) {
+    const size_t row = SP::kPrec == P64 ? (size_t)(c >> 1) * NP * 2 + (c & 1) : (size_t)c * NP;
+    prefetch_l2(b + (row + (SP::kPrec == P64 ? m0 * 2 : m0)) * 16);
+  }
+  if constexpr (SP::kScaled) {
+    if (t == HALF - 1) prefetch_l2(b + (size_t)6 * NP * 16 + m0 * 8);
+  }
+  if (DIR < 0 && t == HALF - 2) {
+    using GP = typename GaugeOf<SP>::type;
+    prefetch_l2(reinterpret_cast<const char*>(gq) + ((size_t)hn * 4 + mu) * GP::kLinkBytes);
+  }
+}
 
 // acc += f (1 - dir gamma_mu) U' v'(x +- mu) for the two slices of a thread,
 // U' = U_mu(x) (dir > 0) or U_mu(x - mu)^+ (dir < 0).
@@ -315,64 +415,10 @@ __device__ __forceinline__ void hop_dir(int nb, int h, int t, size_t NP,
   } else if constexpr (SP::kScaled) {
     f = A::mul(f, IO::scale(v, m, NP));  // per-slice scale of the neighbour site
   }
-  // projection h = P_+ - dir A P_- (in place into P)
-#pragma unroll
-  for (int k = 0; k < 2; k++) {
-    const int pk = partner(MU, k);
-    const int cs = proj_sign(MU, DIR, k);
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      const V pr = P.re[3 * k + a], pi = P.im[3 * k + a];
-      const V mr = M.re[3 * pk + a], mi = M.im[3 * pk + a];
-      if (imag_mu(MU)) {  // P + cs i M
-        P.re[3 * k + a] = cs > 0 ? A::sub(pr, mi) : A::add(pr, mi);
-        P.im[3 * k + a] = cs > 0 ? A::add(pi, mr) : A::sub(pi, mr);
-      } else {            // P + cs M
-        P.re[3 * k + a] = cs > 0 ? A::add(pr, mr) : A::sub(pr, mr);
-        P.im[3 * k + a] = cs > 0 ? A::add(pi, mi) : A::sub(pi, mi);
-      }
-    }
-  }
   Link<T> U;
   if (DIR > 0) GP::load(gp, h, MU, U);
   else GP::load(gq, hn, MU, U);
-  const V fn = A::neg(f);
-  // chi_k = U' h_k; acc_upper(k) += f chi_k; acc_lower(pk) += f rs (i) chi_k
-#pragma unroll
-  for (int k = 0; k < 2; k++) {
-    const int q = partner(MU, k);  // lower row fed by chi_k
-    const int rs = recon_sign(MU, DIR, q);
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      V cr, ci;
-#pragma unroll
-      for (int b = 0; b < 3; b++) {
-        const cplx<T> u = DIR > 0 ? U.u[3 * a + b] : U.u[3 * b + a];
-        const V ur = A::dup(u.re);
-        const V ui = A::dup(DIR > 0 ? u.im : -u.im);
-        const V hr = P.re[3 * k + b], hi = P.im[3 * k + b];
-        if (b == 0) {
-          cr = A::mul(ur, hr);
-          ci = A::mul(ur, hi);
-        } else {
-          cr = A::fma(ur, hr, cr);
-          ci = A::fma(ur, hi, ci);
-        }
-        cr = A::fma(A::neg(ui), hi, cr);
-        ci = A::fma(ui, hr, ci);
-      }
-      acc.re[3 * k + a] = A::fma(f, cr, acc.re[3 * k + a]);
-      acc.im[3 * k + a] = A::fma(f, ci, acc.im[3 * k + a]);
-      const int l = 6 + 3 * q + a;
-      if (imag_mu(MU)) {  // += rs i chi: re -= rs chi_im, im += rs chi_re
-        acc.re[l] = A::fma(rs > 0 ? fn : f, ci, acc.re[l]);
-        acc.im[l] = A::fma(rs > 0 ? f : fn, cr, acc.im[l]);
-      } else {            // += rs chi
-        acc.re[l] = A::fma(rs > 0 ? f : fn, cr, acc.re[l]);
-        acc.im[l] = A::fma(rs > 0 ? f : fn, ci, acc.im[l]);
-      }
-    }
-  }
+  project_mul_acc<SP, MU, DIR>(P, M, U, f, acc);
 }
 
 // Lower-form cyclic bidiagonal multiply: y_k = a_k v_k + b_k v_{k-1 mod L}.
@@ -519,20 +565,22 @@ constexpr int min_blocks() { return sizeof(T) == 8 ? 2 : 4; }
 
 // Common tail of the hopping kernels: 5th-dimension post program, scaling,
 // optional gamma5, local term, store and fused norm.  Every thread of the CTA
-// calls it (it contains __syncthreads).
+// calls it (it contains __syncthreads); threads with part = false (no site of
+// their own) only take part in the barriers and the norm.
 template <class SP, int LS, int POST, int LOC, bool G5, bool NORM>
-__device__ __forceinline__ void epilogue(const Args<typename SP::T>& a, const typename SP::T* coef,
-                                         typename SP::T* site, size_t NP, int h, int t, bool active,
-                                         int rhs, SpinP<typename Pr<typename SP::T>::V>& acc) {
+__device__ __forceinline__ void epilogue_g(const Args<typename SP::T>& a, const typename SP::T* coef,
+                                           typename SP::T* site, size_t NP, int h, int t, bool active,
+                                           bool part, int rhs,
+                                           SpinP<typename Pr<typename SP::T>::V>& acc) {
   using T = typename SP::T;
   using A = Pr<T>;
   using V = typename A::V;
   if (POST != PR_NONE) {
-    put(site + t * kPairStride, acc);
+    if (part) put(site + t * kPairStride, acc);
     __syncthreads();
-    run_prog<T, LS, POST>(site, coef, t);
+    if (part) run_prog<T, LS, POST>(site, coef, t);
     __syncthreads();
-    get(site + t * kPairStride, acc);
+    if (part) get(site + t * kPairStride, acc);
   }
   const V ch = A::dup(a.c_hop);
   const size_t off = rhs * a.stride;
@@ -573,7 +621,7 @@ __device__ __forceinline__ void epilogue(const Args<typename SP::T>& a, const ty
 }
 
 // out = c_hop G post(H v') + c_loc loc(w), two 5th-dimension slices per thread.
-template <class SP, int LS, int PRE, int POST, int LOC, bool G5, bool NORM, int MINB>
+template <class SP, int LS, int PRE, int POST, int LOC, bool G5, bool NORM, int MINB, int PF = 0>
 __global__ void __launch_bounds__(128, MINB) hop_kernel(const Geom g, const Args<typename SP::T> a) {
   using T = typename SP::T;
   using V = typename Pr<T>::V;
@@ -608,16 +656,29 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const Geom g, const Args
           bo[c][k] = __ldg(a.boff + co + c * LS + s0 + k);
         }
     }
-    hop_dir<SP, LS, PRE, 0, +1>(nb0.x, h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
-    hop_dir<SP, LS, PRE, 0, -1>(nb0.y, h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
-    hop_dir<SP, LS, PRE, 1, +1>(nb0.z, h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
-    hop_dir<SP, LS, PRE, 1, -1>(nb0.w, h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
-    hop_dir<SP, LS, PRE, 2, +1>(nb1.x, h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
-    hop_dir<SP, LS, PRE, 2, -1>(nb1.y, h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
-    hop_dir<SP, LS, PRE, 3, +1>(nb1.z, h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
-    hop_dir<SP, LS, PRE, 3, -1>(nb1.w, h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
+    const int nb[8] = {nb0.x, nb0.y, nb0.z, nb0.w, nb1.x, nb1.y, nb1.z, nb1.w};
+    if (PF > 0) {
+#pragma unroll
+      for (int e = 0; e < (PF < 8 ? PF : 8); e++)
+        if (e & 1) prefetch_hop<SP, LS, -1>(nb[e], t, NP, vb, a.gauge_q, e >> 1);
+        else prefetch_hop<SP, LS, +1>(nb[e], t, NP, vb, a.gauge_q, e >> 1);
+    }
+#define DWF_HOP_STEP(D, MU, DIR)                                                         \
+    if (PF > 0 && PF < 8 && D + PF < 8)                                                   \
+      prefetch_hop<SP, LS, ((D + PF) & 1) ? -1 : +1>(nb[(D + PF) & 7], t, NP, vb, a.gauge_q, \
+                                                     ((D + PF) & 7) >> 1);                \
+    hop_dir<SP, LS, PRE, MU, DIR>(nb[D], h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
+    DWF_HOP_STEP(0, 0, +1)
+    DWF_HOP_STEP(1, 0, -1)
+    DWF_HOP_STEP(2, 1, +1)
+    DWF_HOP_STEP(3, 1, -1)
+    DWF_HOP_STEP(4, 2, +1)
+    DWF_HOP_STEP(5, 2, -1)
+    DWF_HOP_STEP(6, 3, +1)
+    DWF_HOP_STEP(7, 3, -1)
+#undef DWF_HOP_STEP
   }
-  epilogue<SP, LS, POST, LOC, G5, NORM>(a, coef, sbuf + j * SST, NP, h, t, active, rhs, acc);
+  epilogue_g<SP, LS, POST, LOC, G5, NORM>(a, coef, sbuf + j * SST, NP, h, t, active, true, rhs, acc);
 }
 
 // out = c * PROG(gamma5^g5in in), site-local, two slices per thread.
@@ -678,6 +739,8 @@ __global__ void __launch_bounds__(128) local_kernel(const Geom g, void* out, con
 }  // namespace hop2
 }  // namespace dwf
 
+#include "dwf_hop_tma.cuh"
+
 namespace dwf {
 namespace hop2 {
 
@@ -685,6 +748,59 @@ inline int block_sites(int Ls) { return 128 / (Ls / 2); }
 
 inline size_t smem_bytes(int Ls, int S, size_t ts) {
   return ts * ((size_t)chain_block(Ls) + (size_t)S * site_stride(Ls));
+}
+
+// Tensor map of a half-field (nrhs fields back to back) as 32-bit words:
+// dim 0 the slice pairs of one row (component or 16-byte chunk row), dim 1 the
+// rows, dim 2 the right-hand sides; the box is one site (Ls/2 pairs) x all rows.
+template <class SP, int LS>
+cudaError_t encode_field_map(CUtensorMap* map, const Geom& g, const void* base, size_t stride,
+                             int nrhs) {
+  using ST = Stage<SP, LS>;
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const size_t NP = (size_t)g.N5 / 2;
+  const cuuint64_t dims[3] = {(cuuint64_t)NP * ST::kWpp, (cuuint64_t)ST::kRows, (cuuint64_t)nrhs};
+  const cuuint64_t row = (cuuint64_t)NP * ST::kWpp * 4;
+  const cuuint64_t strides[2] = {row, (cuuint64_t)(stride ? stride : row * ST::kRows)};
+  const cuuint32_t box[3] = {(cuuint32_t)(LS / 2 * ST::kWpp), (cuuint32_t)ST::kRows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<void*>(base), dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <class SP, int LS>
+constexpr int tma_stages() { return 2; }
+
+template <class SP, int LS, int PRE, int POST, int LOC, bool G5, bool NORM>
+cudaError_t run_tma(const Geom& g, const HopLaunch& L, const Args<typename SP::T>& a, cudaStream_t st) {
+  constexpr int NST = tma_stages<SP, LS>();
+  constexpr int S = kTmaConsumers / (LS / 2);
+  if (((reinterpret_cast<uintptr_t>(L.v) | L.stride) & 15) != 0) return cudaErrorNotSupported;
+  CUtensorMap map;
+  cudaError_t e = encode_field_map<SP, LS>(&map, g, L.v, L.stride, L.nrhs);
+  if (e != cudaSuccess) return e;
+  const size_t smem = tma_smem_bytes<SP, LS, NST>();
+  auto k = hop_tma_kernel<SP, LS, PRE, POST, LOC, G5, NORM, NST, 1>;
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((g.Vh + S - 1) / S, 1, L.nrhs);
+  k<<<grid, kTmaThreads, smem, st>>>(g, a, map, L.wait_budget > 0 ? L.wait_budget : (1LL << 31),
+                                     L.skip_hop);
+  return cudaGetLastError();
 }
 
 template <class SP, int LS, int PRE, int POST, int LOC, bool G5, bool NORM>
@@ -707,7 +823,9 @@ cudaError_t run(const Geom& g, const HopLaunch& L, cudaStream_t st) {
   a.red = L.red ? *L.red : Reduce{};
   a.cstride = L.cstride;
   a.active = L.active;
+  a.err = L.err;
   const int S = block_sites(LS);
+  if (L.use_tma) return run_tma<SP, LS, PRE, POST, LOC, G5, NORM>(g, L, a, st);
   dim3 block(LS / 2, S, 1);
   dim3 grid((g.Vh + S - 1) / S, 1, L.nrhs);
   const size_t smem = smem_bytes(LS, S, sizeof(T));
@@ -731,6 +849,8 @@ cudaError_t dispatch_ls(const Geom& g, const HopLaunch& L, cudaStream_t st) {
   if (L.loc == LOC_DENSE) return cudaErrorNotSupported;
   if (L.pre == PRE_B && L.post_prog == PR_K && L.loc == LOC_NONE && !L.g5out && !norm)
     return run<SP, LS, PRE_B, PR_K, LOC_NONE, false, false>(g, L, st);
+  if (L.pre == PRE_NONE && L.post_prog == PR_K && L.loc == LOC_NONE && !L.g5out && !norm)
+    return run<SP, LS, PRE_NONE, PR_K, LOC_NONE, false, false>(g, L, st);
   if (L.pre == PRE_NONE && L.post_prog == PR_IINV && L.loc == LOC_ID && !L.g5out)
     return norm ? run<SP, LS, PRE_NONE, PR_IINV, LOC_ID, false, true>(g, L, st)
                 : run<SP, LS, PRE_NONE, PR_IINV, LOC_ID, false, false>(g, L, st);

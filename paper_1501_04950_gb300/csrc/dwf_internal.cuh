@@ -85,7 +85,9 @@ struct HopLaunch {
   const void* chain;        // hop2 chain coefficient block in the compute type
   const int* nbr;           // [2 parities][Vh][8] neighbour half indices, bit 31 = sign
   int* err;                 // device flag set when a bounded wait gives up
-  int use_tma;              // 1: stage neighbours through shared memory with bulk copies
+  int use_tma;              // 1: stage neighbours through shared memory with tensor copies
+  long long wait_budget;    // clock cycles a bounded wait may take (0: default, ~1 s)
+  int skip_hop;             // test hook: the staged variant issues no copies for this hop (-1: none)
   size_t cstride;           // elements between right-hand sides of every coefficient
                             // array (pre_diag, pre_off, post, locm, chain); 0: shared
   const int* active;        // per right-hand side: 0 skips it (nullptr: all active)
@@ -147,6 +149,16 @@ cudaError_t launch_px_update(const Geom& g, int prec, int xprec, void* x, void* 
                              const double* a_ptr, const double* num, const double* den,
                              int sstride, int nrhs, size_t stride_x, size_t stride,
                              cudaStream_t s, const int* active);
+// pnew = z + beta p (beta = num / den), bp = B pnew (B of Eq. mobius1 with D_w -> 1,
+// per right-hand side coefficients bdiag/boff [2][Ls] in prec's compute type with
+// stride cstride); with do_x also the deferred x += a_prev p.  p and pnew are
+// different buffers.  Ls even, prec FP32 (x FP32 or FP64) or FP64.
+cudaError_t launch_pxb_update(const Geom& g, int prec, int xprec, void* x, const void* p, void* pnew,
+                              void* bp,
+                              const void* z, const double* a_ptr, const double* num,
+                              const double* den, int sstride, int nrhs, size_t stride_x,
+                              size_t stride, const void* bdiag, const void* boff, size_t cstride,
+                              cudaStream_t s, const int* active, int do_x);
 // x += a p, a = *a_ptr (flush of the deferred solution update).
 cudaError_t launch_x_update(const Geom& g, int prec, int xprec, void* x, const void* p,
                             const double* a_ptr, int sstride, int nrhs, size_t stride_x,
