@@ -166,11 +166,12 @@ int dwf_apply_Dbb(dwf_handle h, void* out, const void* in, int prec, int nrhs, d
  * of DWF_NOALLOC_SCRATCH_BYTES compiled into the library (every GPU that loads
  * the library holds it until exit) instead of handle workspace; no call
  * allocates or frees anything.  Requires nrhs * dwf_field_bytes(prec) <=
- * DWF_NOALLOC_SCRATCH_BYTES, else DWF_ERR_INVALID_ARG.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) and caches
- * it; make that first call before any stream capture.  All calls share the
- * array and each call overwrites it completely, so calls that overlap on the
- * GPU (other streams, other handles) race. */
+ * DWF_NOALLOC_SCRATCH_BYTES, else DWF_ERR_INVALID_ARG.  dwf_create looks up the
+ * array's device address with the handle's device current (create handles
+ * outside any stream capture); calls must be made with that device current,
+ * else DWF_ERR_INVALID_ARG.  All calls share the array and each call
+ * overwrites it completely, so calls that overlap on the GPU (other streams,
+ * other handles) race. */
 #define DWF_NOALLOC_SCRATCH_BYTES (32u << 20)
 int dwf_apply_Dbb_noalloc(dwf_handle h, void* out, const void* in, int prec, int nrhs,
                           dwf_stream s);
@@ -234,6 +235,19 @@ int dwf_apply_overlap(dwf_handle h, const double* src4d, double* out4d, double* 
  * normal residual phi - D_bb^+ D_bb x).  The solve inside dwf_force. */
 int dwf_solve_normal(dwf_handle h, double* x_half, const double* phi_half, dwf_stats* stats,
                      dwf_stream s);
+
+/* Pseudofermion action S = phi^+ (D_bb^+ D_bb)^-1 phi = Re phi^+ X of the
+ * red-black operator of Sec. 3 (Eq. redblack): X = (D_bb^+ D_bb)^-1 phi by the CG
+ * of dwf_solve_normal (the handle's solver options), then S by an FP64 device
+ * reduction over the black half-lattice.
+ *   S        host double output
+ *   phi_half canonical black half-field (device, complex128)
+ *   X_half   X (canonical, device) or NULL if not needed
+ *   stats    solver statistics or NULL
+ * Synchronises (convergence polling).  Errors as dwf_solve_normal; with
+ * DWF_ERR_NOT_CONVERGED, S and X refer to the last iterate. */
+int dwf_action(dwf_handle h, double* S, const double* phi_half, double* X_half, dwf_stats* stats,
+               dwf_stream s);
 
 /* Fermion force of S = phi^+ (D_bb^+ D_bb)^-1 phi.
  *   dSdU     canonical [t][z][y][x][mu][3][3] complex128 device output:

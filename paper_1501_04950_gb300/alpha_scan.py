@@ -69,12 +69,14 @@ def row_coefficients(row, order="concave"):
 
 
 def scan(row, lattice=(16, 16, 16, 32), alphas=None, fields=1, eps=0.5, M5=-1.8, tol=1e-8,
-         precision=None, sources=12, device="cuda", form=0, order="concave"):
-    """Run the scan for one row; returns a dict of per-alpha ratio statistics.
+         precision=None, sources=12, device="cuda", form=0, order="concave", solver=None):
+    """Run the scan for one row; returns a dict of per-alpha ratio statistics and
+    the iteration counts [field][source][alpha].
 
     form selects the red-black operator of Sec. 3 (dwf.SCHUR_*: 0 Eq. redblack,
     1 Eq. redblack1, 2 Eq. redblack1 with scaled rows); order places the
-    Zolotarev coefficients of a Zolotarev row (ORDERS)."""
+    Zolotarev coefficients of a Zolotarev row (ORDERS); solver is a
+    dwf.SOLVER_* (default: inner precision with FP64 reliable updates)."""
     import torch
     from synthetic import gauge_field, point_source4d
     from . import dwf
@@ -95,8 +97,9 @@ def scan(row, lattice=(16, 16, 16, 32), alphas=None, fields=1, eps=0.5, M5=-1.8,
         src = torch.from_numpy(np.concatenate([srcs] * len(alphas))).to(device)
         al = [a for a in alphas for _ in pts]
         # poll every 2 iterations: the counts are exact to 2 instead of 16
+        extra = {} if solver is None else {"solver": solver}
         op = dwf.DWF(lattice, Ls, M5, mass, 1.0, b, c, rel_tol=tol, precision_inner=precision,
-                     check_every=2, schur_form=form)
+                     check_every=2, schur_form=form, **extra)
         op.load_gauge(U)
         prop = torch.empty_like(src)
         st = op.cgne_solve(src, prop, nrhs=len(al), alphas=al)
@@ -115,6 +118,7 @@ def scan(row, lattice=(16, 16, 16, 32), alphas=None, fields=1, eps=0.5, M5=-1.8,
         "alphas": alphas, "ratio_mean": mean.tolist(), "ratio_std": std.tolist(),
         "iterations_alpha1_mean": float(n[:, :, one].mean()),
         "best_alpha": alphas[best], "speedup_percent": 100.0 * (1.0 - mean[best]),
+        "iterations": n.astype(int).tolist(),
         "seconds": time.perf_counter() - t0,
     }
 

@@ -198,6 +198,7 @@ struct dwf_ctx {
   std::vector<double> b, c;
   dwf_options opt{};
   int device = 0;
+  void* noalloc_scratch = nullptr;               // device address of the static scratch array
   std::string err;
   std::map<std::pair<double, double>, MatSet> mats;
   void* gauge[3] = {nullptr, nullptr, nullptr};  // FP64, FP32, FP16
@@ -205,8 +206,8 @@ struct dwf_ctx {
   int* dev_err = nullptr;                        // set by a kernel whose bounded wait gave up
   int use_tma = 0;                               // DWF_TMA: tensor-copy staged tuned kernels
   long long wait_budget = 0;                     // DWF_WAIT_BUDGET: clock cycles per bounded wait
-  int skip_hop = -1;                             // DWF_TEST_SKIP_HOP: staged kernels issue no
-                                                 // copies for this hop (timeout test hook)
+  int skip_hop = -1;                             // DWF_TEST_SKIP_HOP: the first staged launch
+                                                 // issues no copies for this hop (timeout test)
   bool fused_cg = true;                          // DWF_UNFUSED_CG unset: fused CG BLAS steps
   bool bp_fused = true;                          // DWF_NO_BP_FUSED unset: p update forms B p
   int check = 16;                                // effective iterations between polls
@@ -406,7 +407,7 @@ HopLaunch base_hop(dwf_ctx* h, int prec, int p, int nrhs, size_t stride) {
   L.err = h->dev_err;
   L.use_tma = h->use_tma;
   L.wait_budget = h->wait_budget;
-  L.skip_hop = h->skip_hop;
+  L.skip_hop = &h->skip_hop;  // one-shot test hook, consumed by the first staged launch
   return L;
 }
 
@@ -1333,15 +1334,20 @@ int dwf_create(dwf_handle* out, const int lattice[4], int Ls, double M5, double 
   // DWF_GENERIC_KERNELS=1 selects the generic (any Ls, dense 5th-dimension)
   // kernels instead of the tuned ones; used to cross-check the two paths.
   g_disable_tuned = std::getenv("DWF_GENERIC_KERNELS") != nullptr;
-  // DWF_TMA=1 stages the neighbour blocks of the tuned FP32/16-bit kernels
-  // through shared memory with cp.async.bulk (measured slower than direct
-  // loads on the 16^3x32 workload; kept as an alternative staging strategy).
+  // DWF_TMA=1 stages the neighbour blocks of the tuned kernels through shared
+  // memory with tensor copies (measured slower than direct loads on the
+  // 16^3x32 workload; kept as an alternative staging strategy).
   h->use_tma = std::getenv("DWF_TMA") != nullptr;
   h->bp_fused = std::getenv("DWF_NO_BP_FUSED") == nullptr;
   if (const char* e = std::getenv("DWF_WAIT_BUDGET")) h->wait_budget = std::atoll(e);
   if (const char* e = std::getenv("DWF_TEST_SKIP_HOP")) h->skip_hop = std::atoi(e);
   h->fused_cg = std::getenv("DWF_UNFUSED_CG") == nullptr;
   cudaGetDevice(&h->device);
+  // address of the static scratch of dwf_apply_Dbb_noalloc on this device
+  if (noalloc_scratch_address(&h->noalloc_scratch) != cudaSuccess) {
+    cudaGetLastError();
+    h->noalloc_scratch = nullptr;
+  }
   if (cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     delete h;
@@ -1539,6 +1545,40 @@ int dwf_solve_normal(dwf_handle h, double* x_half, const double* phi_half, dwf_s
   if (rc && rc != DWF_ERR_NOT_CONVERGED) return rc;
   KLAUNCH(h, launch_unpack_half(h->g, P64, x_half, W.x_hi, 1, st));
   CUCHK(h, cudaStreamSynchronize(st));
+  sk.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = sk;
+  return rc;
+}
+
+int dwf_action(dwf_handle h, double* S, const double* phi_half, double* X_half, dwf_stats* stats,
+               dwf_stream s) {
+  if (!h || !S || !phi_half) return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  if (!h->gauge_loaded) return fail(h, DWF_ERR_STATE, "gauge field not loaded");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  int rc;
+  if ((rc = ensure_reduce(h, 1))) return rc;
+  int prec;
+  double delta;
+  bool restart;
+  solver_params(h, &prec, &delta, &restart);
+  SolveWork W;
+  if ((rc = alloc_solve_work(h, prec, W))) return rc;
+  void* t64b;
+  if ((rc = get_ws(h, "t64b", field_bytes(h->g, P64), &t64b))) return rc;
+  MatSet* ms;
+  if ((rc = build_matset(h, h->alpha, h->m, &ms))) return rc;
+  auto t0 = std::chrono::steady_clock::now();
+  KLAUNCH(h, launch_pack_half(h->g, P64, W.b_hi, phi_half, 1, st));
+  dwf_stats sk{};
+  rc = cgnormal_solve(h, *ms, prec, h->opt.rel_tol, h->opt.maxiter, delta, W, t64b, &sk, st);
+  if (rc && rc != DWF_ERR_NOT_CONVERGED) return rc;
+  // S = Re phi^+ X, FP64 device reduction over the black half-lattice
+  Reduce red = make_reduce(h, 0, S_T0);
+  KLAUNCH(h, launch_dot_re64(h->g, W.b_hi, W.x_hi, 1, field_bytes(h->g, P64), &red, st));
+  if (X_half) KLAUNCH(h, launch_unpack_half(h->g, P64, X_half, W.x_hi, 1, st));
+  int rc2;
+  if ((rc2 = sync_read(h, 1, st))) return rc2;
+  *S = h->pinned[S_T0];
   sk.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = sk;
   return rc;
@@ -1788,13 +1828,20 @@ namespace dwf {
 
 int set_error(dwf_handle h, int code, const char* msg) { return fail(h, code, msg); }
 
-// D_bb apply with a caller-supplied red intermediate field of at least
-// nrhs * field_bytes(prec) bytes; allocates nothing (the handle's matrices for
-// its own alpha and m exist since dwf_create).
-int apply_dbb_with_scratch(dwf_handle h, void* out, const void* in, int prec, int nrhs,
-                           void* scratch, size_t scratch_bytes, cudaStream_t s) {
+// D_bb apply with the static scratch array as the red intermediate field (at
+// least nrhs * field_bytes(prec) bytes); allocates nothing (the handle's
+// matrices for its own alpha and m exist since dwf_create).
+int apply_dbb_noalloc(dwf_handle h, void* out, const void* in, int prec, int nrhs,
+                      size_t scratch_bytes, cudaStream_t s) {
   if (!h || !out || !in || !valid_prec(prec) || nrhs < 1 || out == in)
     return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != h->device)
+    return fail(h, DWF_ERR_INVALID_ARG,
+                "dwf_apply_Dbb_noalloc: the current device is not the handle's device");
+  if (!h->noalloc_scratch)
+    return fail(h, DWF_ERR_CUDA, "the static scratch array has no device address on this device");
+  void* scratch = h->noalloc_scratch;
   if (!h->gauge_loaded) return fail(h, DWF_ERR_STATE, "gauge field not loaded");
   const size_t need = field_bytes(h->g, prec) * (size_t)nrhs;
   if (need > scratch_bytes)

@@ -341,35 +341,6 @@ __device__ __forceinline__ void project_mul_acc(HalfP<typename Pr<typename SP::T
   }
 }
 
-// L2 prefetch of the neighbour data of one hop: the site's slice-pair block of
-// every spinor component (one 128-byte line per component at Ls = 16), spread
-// over the Ls/2 threads of the site, and the link of a backward hop.  Issued a
-// few hops ahead so that first touches of DRAM overlap the current hop.
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-template <class SP, int LS, int DIR>
-__device__ __forceinline__ void prefetch_hop(int nb, int t, size_t NP, const void* v, const void* gq,
-                                             int mu) {
-  constexpr int HALF = LS / 2;
-  constexpr int kComp = SP::kPrec == P64 ? 24 : (SP::kScaled ? 6 : 12);  // 16-byte chunk rows
-  const int hn = nb & 0x7fffffff;
-  const size_t m0 = (size_t)hn * HALF;
-  const char* b = reinterpret_cast<const char*>(v);
-#pragma unroll
-  for (int c = t; c < kComp; c += HALF) {
-    const size_t row = SP::kPrec == P64 ? (size_t)(c >> 1) * NP * 2 + (c & 1) : (size_t)c * NP;
-    prefetch_l2(b + (row + (SP::kPrec == P64 ? m0 * 2 : m0)) * 16);
-  }
-  if constexpr (SP::kScaled) {
-    if (t == HALF - 1) prefetch_l2(b + (size_t)6 * NP * 16 + m0 * 8);
-  }
-  if (DIR < 0 && t == HALF - 2) {
-    using GP = typename GaugeOf<SP>::type;
-    prefetch_l2(reinterpret_cast<const char*>(gq) + ((size_t)hn * 4 + mu) * GP::kLinkBytes);
-  }
-}
-
 // acc += f (1 - dir gamma_mu) U' v'(x +- mu) for the two slices of a thread,
 // U' = U_mu(x) (dir > 0) or U_mu(x - mu)^+ (dir < 0).
 template <class SP, int LS, int PRE, int MU, int DIR>
@@ -621,7 +592,7 @@ __device__ __forceinline__ void epilogue_g(const Args<typename SP::T>& a, const 
 }
 
 // out = c_hop G post(H v') + c_loc loc(w), two 5th-dimension slices per thread.
-template <class SP, int LS, int PRE, int POST, int LOC, bool G5, bool NORM, int MINB, int PF = 0>
+template <class SP, int LS, int PRE, int POST, int LOC, bool G5, bool NORM, int MINB>
 __global__ void __launch_bounds__(128, MINB) hop_kernel(const Geom g, const Args<typename SP::T> a) {
   using T = typename SP::T;
   using V = typename Pr<T>::V;
@@ -657,26 +628,14 @@ __global__ void __launch_bounds__(128, MINB) hop_kernel(const Geom g, const Args
         }
     }
     const int nb[8] = {nb0.x, nb0.y, nb0.z, nb0.w, nb1.x, nb1.y, nb1.z, nb1.w};
-    if (PF > 0) {
-#pragma unroll
-      for (int e = 0; e < (PF < 8 ? PF : 8); e++)
-        if (e & 1) prefetch_hop<SP, LS, -1>(nb[e], t, NP, vb, a.gauge_q, e >> 1);
-        else prefetch_hop<SP, LS, +1>(nb[e], t, NP, vb, a.gauge_q, e >> 1);
-    }
-#define DWF_HOP_STEP(D, MU, DIR)                                                         \
-    if (PF > 0 && PF < 8 && D + PF < 8)                                                   \
-      prefetch_hop<SP, LS, ((D + PF) & 1) ? -1 : +1>(nb[(D + PF) & 7], t, NP, vb, a.gauge_q, \
-                                                     ((D + PF) & 7) >> 1);                \
-    hop_dir<SP, LS, PRE, MU, DIR>(nb[D], h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
-    DWF_HOP_STEP(0, 0, +1)
-    DWF_HOP_STEP(1, 0, -1)
-    DWF_HOP_STEP(2, 1, +1)
-    DWF_HOP_STEP(3, 1, -1)
-    DWF_HOP_STEP(4, 2, +1)
-    DWF_HOP_STEP(5, 2, -1)
-    DWF_HOP_STEP(6, 3, +1)
-    DWF_HOP_STEP(7, 3, -1)
-#undef DWF_HOP_STEP
+    hop_dir<SP, LS, PRE, 0, +1>(nb[0], h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
+    hop_dir<SP, LS, PRE, 0, -1>(nb[1], h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
+    hop_dir<SP, LS, PRE, 1, +1>(nb[2], h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
+    hop_dir<SP, LS, PRE, 1, -1>(nb[3], h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
+    hop_dir<SP, LS, PRE, 2, +1>(nb[4], h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
+    hop_dir<SP, LS, PRE, 2, -1>(nb[5], h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
+    hop_dir<SP, LS, PRE, 3, +1>(nb[6], h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
+    hop_dir<SP, LS, PRE, 3, -1>(nb[7], h, t, NP, bd, bo, vb, a.gauge_p, a.gauge_q, acc);
   }
   epilogue_g<SP, LS, POST, LOC, G5, NORM>(a, coef, sbuf + j * SST, NP, h, t, active, true, rhs, acc);
 }
@@ -798,8 +757,13 @@ cudaError_t run_tma(const Geom& g, const HopLaunch& L, const Args<typename SP::T
     attr = true;
   }
   dim3 grid((g.Vh + S - 1) / S, 1, L.nrhs);
+  int skip = -1;
+  if (L.skip_hop && *L.skip_hop >= 0) {
+    skip = *L.skip_hop;
+    *L.skip_hop = -1;
+  }
   k<<<grid, kTmaThreads, smem, st>>>(g, a, map, L.wait_budget > 0 ? L.wait_budget : (1LL << 31),
-                                     L.skip_hop);
+                                     skip);
   return cudaGetLastError();
 }
 

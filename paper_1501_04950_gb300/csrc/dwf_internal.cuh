@@ -87,7 +87,8 @@ struct HopLaunch {
   int* err;                 // device flag set when a bounded wait gives up
   int use_tma;              // 1: stage neighbours through shared memory with tensor copies
   long long wait_budget;    // clock cycles a bounded wait may take (0: default, ~1 s)
-  int skip_hop;             // test hook: the staged variant issues no copies for this hop (-1: none)
+  int* skip_hop;            // test hook: the next staged launch issues no copies for hop
+                            // *skip_hop (>= 0), then sets it to -1; nullptr: none
   size_t cstride;           // elements between right-hand sides of every coefficient
                             // array (pre_diag, pre_off, post, locm, chain); 0: shared
   const int* active;        // per right-hand side: 0 skips it (nullptr: all active)
@@ -233,7 +234,10 @@ cudaError_t launch_force(const Geom& g, double* out, const void* eta1, const voi
 
 typedef struct dwf_ctx* dwf_handle_internal;
 namespace dwf {
-int apply_dbb_with_scratch(dwf_handle_internal h, void* out, const void* in, int prec, int nrhs,
-                           void* scratch, size_t scratch_bytes, cudaStream_t s);
+// D_bb apply using the static scratch array whose address the handle looked up
+// at creation (dwf_noalloc.cu); rejects a current device other than the handle's.
+int apply_dbb_noalloc(dwf_handle_internal h, void* out, const void* in, int prec, int nrhs,
+                      size_t scratch_bytes, cudaStream_t s);
+cudaError_t noalloc_scratch_address(void** out);
 int set_error(dwf_handle_internal h, int code, const char* msg);
 }  // namespace dwf

@@ -8,8 +8,6 @@
 // not acceptable.  This entry point instead uses the file-scope device array
 // g_noalloc_scratch below, of DWF_NOALLOC_SCRATCH_BYTES, which every GPU that
 // loads the library holds until the process exits.
-#include <mutex>
-
 #include "../../include/dwf.h"
 #include "dwf_internal.cuh"
 
@@ -21,37 +19,19 @@ namespace {
 // race on its contents.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[DWF_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of g_noalloc_scratch on the current device.  In host code the
-// array's name is only a stand-in, so the address is looked up once per device
-// (with that device current) and cached.
-cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
-  return cudaSuccess;
-}
-
 }  // namespace
+
+namespace dwf {
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// array's name is only a stand-in, so dwf_create looks the address up once,
+// with the handle's device current, and keeps it in the handle.
+cudaError_t noalloc_scratch_address(void** out) {
+  return cudaGetSymbolAddress(out, g_noalloc_scratch);
+}
+}  // namespace dwf
 
 extern "C" int dwf_apply_Dbb_noalloc(dwf_handle h, void* out, const void* in, int prec, int nrhs,
                                      dwf_stream s) {
-  void* scratch = nullptr;
-  cudaError_t e = scratch_address(&scratch);
-  if (e != cudaSuccess)
-    return dwf::set_error(h, DWF_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
-  return dwf::apply_dbb_with_scratch(h, out, in, prec, nrhs, scratch, DWF_NOALLOC_SCRATCH_BYTES,
-                                     reinterpret_cast<cudaStream_t>(s));
+  return dwf::apply_dbb_noalloc(h, out, in, prec, nrhs, DWF_NOALLOC_SCRATCH_BYTES,
+                                reinterpret_cast<cudaStream_t>(s));
 }

@@ -51,7 +51,7 @@ EXPORTS = [
     "dwf_default_options", "dwf_create", "dwf_destroy", "dwf_last_error", "dwf_field_bytes",
     "dwf_load_gauge", "dwf_pack_half", "dwf_unpack_half", "dwf_apply_Dbb", "dwf_apply_Dbb_dag",
     "dwf_apply_dalpha", "dwf_cgne_solve", "dwf_solve_normal", "dwf_force",
-    "dwf_apply_Dbb_noalloc", "dwf_apply_overlap",
+    "dwf_apply_Dbb_noalloc", "dwf_apply_overlap", "dwf_action",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -79,6 +79,7 @@ def load_library(path: str = LIB_PATH):
         "dwf_apply_overlap": (I, [P, P, P, P, I, ctypes.POINTER(D), ctypes.POINTER(Stats), P]),
         "dwf_solve_normal": (I, [P, P, P, ctypes.POINTER(Stats), P]),
         "dwf_force": (I, [P, P, P, P, I, P]),
+        "dwf_action": (I, [P, ctypes.POINTER(D), P, P, ctypes.POINTER(Stats), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -216,6 +217,14 @@ class DWF:
         self._check(self.lib.dwf_solve_normal(self.h, _ptr(x_half), _ptr(phi_half), ctypes.byref(st),
                                               _stream()))
         return st.as_dict()
+
+    def action(self, phi_half, X_half=None):
+        """S = Re phi^+ (D_bb^+ D_bb)^-1 phi (dwf_action); returns (S, stats)."""
+        S = ctypes.c_double()
+        st = Stats()
+        self._check(self.lib.dwf_action(self.h, ctypes.byref(S), _ptr(phi_half), _ptr(X_half),
+                                        ctypes.byref(st), _stream()))
+        return S.value, st.as_dict()
 
     def force(self, dSdU, phi_half, X_half=None, projected=False):
         self._check(self.lib.dwf_force(self.h, _ptr(dSdU), _ptr(phi_half), _ptr(X_half),

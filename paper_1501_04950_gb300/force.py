@@ -1,7 +1,7 @@
 """torch.autograd.Function for the fermion action S = phi^+ (D_bb^+ D_bb)^-1 phi.
 
-The forward pass solves (D_bb^+ D_bb) X = phi with libdwf's CG
-(dwf_solve_normal) and returns S = Re phi^+ X.  The backward pass asks libdwf
+The forward pass asks libdwf for S = Re phi^+ X with X = (D_bb^+ D_bb)^-1 phi
+(dwf_action: CG and an FP64 device reduction).  The backward pass asks libdwf
 for the link gradient (dwf_force), recomputing X instead of keeping any solver
 history; the gradient of a complex tensor follows torch's convention
 dS/dRe U + i dS/dIm U, which is what dwf_force returns.
@@ -19,12 +19,11 @@ class FermionAction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, U, phi, op):
         op.load_gauge(U.detach())
-        X = torch.empty_like(phi)
-        stats = op.solve_normal(X, phi)
+        S, stats = op.action(phi)
         ctx.op = op
         ctx.save_for_backward(U, phi)
         ctx.stats = stats
-        return torch.real(torch.vdot(phi.reshape(-1), X.reshape(-1)))
+        return torch.tensor(S, dtype=torch.float64, device=phi.device)
 
     @staticmethod
     def backward(ctx, grad_out):
