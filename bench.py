@@ -13,10 +13,16 @@ value: D_bb-apply bytes per second over the whole timed solve, i.e.
 (D_bb + D_bb^+ applies) x algorithmic bytes per apply / wall time of the steps,
 with the two-pass byte model 120 w_s + 16 r w_g / Ls per 5D half-site
 (w_s, w_g bytes per real of spinor and gauge, r = 18 reals per link).
-roofline: the D_bb apply (hop pass A + pass B) timed with CUDA events on the
-solver's stream inside the timed region, against the measured HBM copy peak.
+roofline: the D_bb apply of the CG (hop pass A on B p, which the p update forms,
++ pass B) timed with CUDA events on the solver's stream inside the timed region,
+against the measured HBM copy peak.  alu: the same applies as GFLOP/s with the
+minimum flop count per site, against the FP32 FFMA throughput measured in the
+same run (libdwf_probe).  accuracy (outside the timed region): the 5D residual of
+the workload's solution at 24 sampled sites by the single-site oracle, and the
+4^4 propagator error against the oracle's own solve.
 cpu_baseline / --impl reference: the FP64 numpy oracle's D_bb apply on a
-bounded sample (8^3x16 sub-lattice, same parameters), with the FP64 byte model.
+bounded sample (8^3x16 sub-lattice, same parameters), with the FP64 byte model;
+also on all host cores (one process per core) and the oracle's 4^4 CGNE time.
 """
 from __future__ import annotations
 
@@ -47,6 +53,93 @@ GAUGE_REALS = 18
 def bytes_per_site(ws, wg, Ls, r=GAUGE_REALS):
     """Two-pass algorithmic bytes of one D_bb apply per 5D half-site."""
     return 120 * ws + 16 * r * wg / Ls
+
+
+# Minimum floating-point work of one D_bb apply per 5D half-site: two Wilson hops
+# (1320 each, the conventional count: projection, SU(3) multiply, reconstruction
+# over 8 directions) plus the 5th-dimension factors B, K = B I^-1 and I^-1 by
+# their cyclic-bidiagonal recurrences and the final axpy.
+FLOP_PER_SITE = 3120
+
+
+def probe_fma_peaks(kinds=(1, 0), iters=None):
+    """Measured FMA throughput (TFLOP/s) on the current GPU: 1 FP32 FFMA, 0 FP64
+    DFMA, 2 paired FP32 FFMA2, 3 FP16 HFMA2 (libdwf_probe.so, independent chains)."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_1501_04950_gb300", "libdwf_probe.so")
+    lib = ctypes.CDLL(path)
+    lib.dwf_probe_fma.restype = ctypes.c_int
+    lib.dwf_probe_fma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]
+    names = {0: "fp64_dfma", 1: "fp32_ffma", 2: "fp32_ffma2", 3: "fp16_hfma2"}
+    default_iters = {0: 20000, 1: 200000, 2: 100000, 3: 200000}
+    out = {}
+    for k in kinds:
+        tf, ms = ctypes.c_double(), ctypes.c_double()
+        rc = lib.dwf_probe_fma(k, (iters or default_iters)[k], ctypes.byref(tf), ctypes.byref(ms))
+        if rc != 0:
+            raise RuntimeError("FMA probe %d failed (CUDA error %d)" % (k, rc))
+        out[names[k]] = round(tf.value, 3)
+    return out
+
+
+def sampled_accuracy(U, src, sol5d, prop, nsites=24, seed=5):
+    """5D residual |rhs - D_alpha psi| at sampled 4D sites of a returned solution
+    (single-site oracle) over the RMS |rhs| of those sites, and the largest
+    deviation of the returned z_1 from P_- psi_1 + P_+ psi_Ls there."""
+    import oracle as O
+    from oracle.lattice import P_MINUS, P_PLUS
+    from oracle.pointwise import PointwiseDalpha
+    sysm = O.DWFSystem(LATTICE, LS, M5, MASS, 1.0, np.full(LS, B), np.full(LS, C), U)
+    pw = PointwiseDalpha(sysm)
+    cache = {}
+
+    def psi_at(c):
+        if c not in cache:
+            x, y, z, t = c
+            cache[c] = sol5d[:, t, z, y, x].cpu().numpy()
+        return cache[c]
+
+    rng = np.random.default_rng(seed)
+    res, ref, zdev = [], [], 0.0
+    for _ in range(nsites):
+        site = tuple(int(rng.integers(0, n)) for n in LATTICE)
+        x, y, z, t = site
+        rhs = pw.rhs_at(src, site)
+        res.append(np.linalg.norm(pw.apply_at(psi_at, site) - rhs))
+        ref.append(np.linalg.norm(rhs))
+        ps = psi_at(site)
+        z1 = P_MINUS @ ps[0] + P_PLUS @ ps[LS - 1]
+        zdev = max(zdev, float(np.abs(prop[t, z, y, x].cpu().numpy() - z1).max() / np.abs(z1).max()))
+    return {"sites": nsites, "resid5d_over_rms_rhs": float(max(res) / np.sqrt(np.mean(np.square(ref)))),
+            "z1_extraction_rel_dev": zdev}
+
+
+def config1_propagator_error():
+    """4^4, Ls = 8 Shamir, M5 = -1.8, m = 0.01, eps = 0.3, even-wall Gaussian source:
+    the mixed FP32/FP64 GPU solve to 1e-10 against the oracle's FP64 solve to 1e-12,
+    max |z_1 - z_1^oracle| / max |z_1^oracle|, and the oracle's CGNE time."""
+    import torch
+    import oracle as O
+    from paper_1501_04950_gb300 import dwf
+    from synthetic import gauge_field, gaussian_source4d
+    L, Ls = (4, 4, 4, 4), 8
+    U = gauge_field(L, 0.3, seed=0)
+    src = gaussian_source4d(L, seed=1, even_only=True)
+    sysm = O.DWFSystem(L, Ls, M5, 0.01, 1.0, np.ones(Ls), np.zeros(Ls), U)
+    t0 = time.perf_counter()
+    ref = O.solve_propagator(sysm, src, tol=1e-12)
+    t_oracle = time.perf_counter() - t0
+    op = dwf.DWF(L, Ls, M5, 0.01, 1.0, np.ones(Ls), np.zeros(Ls))
+    op.load_gauge(torch.from_numpy(U).cuda())
+    s = torch.from_numpy(src).cuda()
+    prop = torch.empty_like(s)
+    st = op.cgne_solve(s, prop)[0]
+    op.close()
+    err = float(np.abs(prop.cpu().numpy() - ref["z1"]).max() / np.abs(ref["z1"]).max())
+    return {"workload": "4^4 Ls=8 Shamir m=0.01 eps=0.3, even-wall source", "z1_rel_error": err,
+            "true_resid": st["true_resid"], "oracle_iterations": ref["iterations"],
+            "oracle_cgne_seconds": t_oracle}
 
 
 def workload_name(alpha):
@@ -172,6 +265,33 @@ def oracle_apply_sample(reps):
     n5 = np.prod(SAMPLE_LATTICE) // 2 * LS
     gbs = n5 * bytes_per_site(8, 8, LS) / statistics.median(times) / 1e9
     return gbs, times
+
+
+def _oracle_worker(reps):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    if reps == 0:  # start-up: imports only
+        import oracle  # noqa: F401
+        import synthetic  # noqa: F401
+        return 0.0
+    gbs, times = oracle_apply_sample(reps)
+    return sum(times)
+
+
+def oracle_apply_all_cores(reps=2):
+    """The oracle's FP64 D_bb apply on the sample lattice in one single-threaded
+    process per host core (spawned), all at once: aggregate GB/s and cores."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    n5 = np.prod(SAMPLE_LATTICE) // 2 * LS
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_worker, [0] * cores)  # start-up and imports, not timed
+        t0 = time.perf_counter()
+        pool.map(_oracle_worker, [reps] * cores)
+        dt = time.perf_counter() - t0
+    return cores * reps * n5 * bytes_per_site(8, 8, LS) / dt / 1e9, cores, dt
 
 
 def run_reference(args, rank):
@@ -325,6 +445,75 @@ def run_zolotarev(args):
     return row
 
 
+def sign_error(a, xmin=0.05, xmax=6.0, n=20001):
+    """max |1 - R(x)| on [xmin, xmax] of the rational sign approximation
+    R = [prod(1 + a_i x) - prod(1 - a_i x)] / [prod(1 + a_i x) + prod(1 - a_i x)]
+    (the polar form of App. A) for coefficients a_i = b_i + c_i."""
+    x = np.geomspace(xmin, xmax, n)
+    ax = np.outer(x, np.asarray(a, dtype=np.float64))
+    lp = np.log(np.abs(1.0 + ax)).sum(axis=1)
+    lm = np.log(np.abs(1.0 - ax)).sum(axis=1)
+    r = np.exp(lm - lp) * np.prod(np.sign(1.0 - ax), axis=1)
+    return float(np.max(np.abs(1.0 - (1.0 - r) / (1.0 + r))))
+
+
+def run_zolo_projection(args, lattice=(16, 16, 16, 32), ls_zolo=8, ls_mobius=32, mass=0.06,
+                        alphas=(0.3, 0.4, 0.5, 0.6, 0.8, 1.0), tol=1e-8):
+    """Sec. 3 projects that Zolotarev coefficients in concave order together with
+    alpha make the solve "2 to 3 times faster".  Measured here: time and
+    iterations to the FP64 true residual `tol` (FP32 inner CG) of one point source
+    for (1) Zolotarev, concave, best alpha of a scan; (2) the same at alpha = 1;
+    (3) Mobius b = 1.5, c = 0.5 at alpha = 1 with Ls chosen for at least the same
+    sign-function accuracy on [0.05, 6]."""
+    import torch
+    from paper_1501_04950_gb300 import dwf
+    from synthetic import gauge_field, point_source4d, zolotarev_mobius
+    dev = torch.device("cuda", 0)
+    U = torch.from_numpy(gauge_field(lattice, EPS, seed=0)).to(dev)
+    src1 = torch.from_numpy(point_source4d(lattice, 0, 0)).to(dev)
+    bz, cz, _, _ = zolotarev_mobius(ls_zolo, 0.05, 6.0)
+    bm, cm = np.full(ls_mobius, B), np.full(ls_mobius, C)
+    out = {"workload": "%s Zolotarev Ls=%d (concave) vs Mobius b=1.5 c=0.5 Ls=%d, M5=-1.8 m=%g "
+                       "eps=0.5, point source, FP32 inner CG to FP64 true residual %g"
+                       % ("x".join(map(str, lattice)), ls_zolo, ls_mobius, mass, tol),
+           "sign_error_zolotarev": sign_error(bz + cz), "sign_error_mobius": sign_error(bm + cm)}
+    # alpha scan of the Zolotarev operator (one batched call, iteration counts exact to 2)
+    op = dwf.DWF(lattice, ls_zolo, M5, mass, 1.0, bz, cz, rel_tol=tol, check_every=2)
+    op.load_gauge(U)
+    srcn = src1.unsqueeze(0).repeat(len(alphas), *([1] * src1.dim())).contiguous()
+    prop = torch.empty_like(srcn)
+    st = op.cgne_solve(srcn, prop, nrhs=len(alphas), alphas=list(alphas))
+    op.close()
+    its = [x["iterations"] for x in st]
+    best = alphas[int(np.argmin(its))]
+    out["zolotarev_alpha_scan"] = {"alphas": list(alphas), "iterations": its}
+
+    def timed(Ls, b, c, alpha, reps=2):
+        o = dwf.DWF(lattice, Ls, M5, mass, alpha, b, c, rel_tol=tol)
+        o.load_gauge(U)
+        p = torch.empty_like(src1)
+        o.cgne_solve(src1, p)  # first-use costs, not timed
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            s = o.cgne_solve(src1, p)[0]
+        torch.cuda.synchronize()
+        o.close()
+        return {"Ls": Ls, "alpha": alpha, "iterations": s["iterations"],
+                "seconds": (time.perf_counter() - t0) / reps, "true_resid": s["true_resid"],
+                "iterations_x_Ls": s["iterations"] * Ls}
+
+    out["zolotarev_best_alpha"] = timed(ls_zolo, bz, cz, best)
+    out["zolotarev_alpha1"] = timed(ls_zolo, bz, cz, 1.0)
+    out["mobius_alpha1"] = timed(ls_mobius, bm, cm, 1.0)
+    m, z = out["mobius_alpha1"], out["zolotarev_best_alpha"]
+    out["factor_time"] = m["seconds"] / z["seconds"]
+    out["factor_iterations_x_Ls"] = m["iterations_x_Ls"] / z["iterations_x_Ls"]
+    out["factor_alpha_only"] = out["zolotarev_alpha1"]["seconds"] / z["seconds"]
+    print(json.dumps(out), flush=True)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,6 +534,11 @@ def main():
                          "12 spin-colour point sources x alpha in {1, 1.5} per lattice")
     ap.add_argument("--zolotarev", action="store_true",
                     help="Zolotarev 24^3x48, Ls=12, m=0.005 solve per inner precision")
+    ap.add_argument("--zolo-projection", action="store_true",
+                    help="Sec. 3 projection: Zolotarev + alpha against Mobius at matched "
+                         "sign-function accuracy (time and iterations to 1e-8)")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measured FMA throughput of the GPU (FP64, FP32, paired FP32, FP16)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -363,6 +557,13 @@ def main():
         return
     if args.zolotarev:
         run_zolotarev(args)
+        return
+    if args.zolo_projection:
+        lat = tuple(int(v) for v in args.lattice.split(",")) if args.lattice else (16, 16, 16, 32)
+        run_zolo_projection(args, lattice=lat)
+        return
+    if args.peaks:
+        print(json.dumps({"fma_tflops": probe_fma_peaks(kinds=(0, 1, 2, 3))}), flush=True)
         return
 
     import torch
@@ -458,6 +659,25 @@ def main():
                 "true_resid": s64["true_resid"]}
         op64.close()
 
+    # accuracy of the timed workload's solution (outside the timed region): one
+    # more solve with the full 5D solution, checked at sampled sites
+    accuracy = None
+    if rank == 0:
+        sol5d = torch.empty((LS,) + tuple(src.shape), dtype=torch.complex128, device=dev)
+        op.cgne_solve(src, prop, sol5d)
+        torch.cuda.synchronize()
+        accuracy = sampled_accuracy(U.cpu().numpy(), src.cpu().numpy(), sol5d, prop)
+        del sol5d
+        accuracy["config1"] = config1_propagator_error()
+    alu = None
+    if rank == 0:
+        pk = probe_fma_peaks(kinds=(1, 0))
+        gflops = n_apply * n5 * FLOP_PER_SITE / (apply_ms / 1e3) / 1e9 if apply_ms > 0 else None
+        alu = {"flop_per_site": FLOP_PER_SITE, "gflops": gflops, "peak_tflops": pk["fp32_ffma"],
+               "frac": gflops / (pk["fp32_ffma"] * 1e3) if gflops else None,
+               "peak_kind": "measured FP32 FFMA (libdwf_probe, this run)",
+               "fp64_dfma_tflops": pk["fp64_dfma"]}
+
     sweep = None
     if not args.no_sweep:
         # config-2 alpha sweep: one batched call per solver, the same source for every alpha
@@ -484,9 +704,16 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         gbs, times = oracle_apply_sample(3)
+        all_gbs, cores, dt_all = oracle_apply_all_cores(reps=2)
         cpu = {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                "sample": "median of 3 FP64 D_bb applies on an 8^3x16, Ls=16 sub-lattice "
-                         "(%.1f s each)" % statistics.median(times)}
+                         "(%.1f s each)" % statistics.median(times),
+               "all_cores": {"value": all_gbs, "unit": "GB/s", "cores": cores,
+                             "sample": "2 applies of the same sub-lattice in each of %d "
+                                       "single-threaded processes at once (%.1f s)"
+                                       % (cores, dt_all)},
+               "config1_cgne_seconds": accuracy["config1"]["oracle_cgne_seconds"],
+               "config1_cgne_note": "oracle FP64 CGNR to 1e-12 on 4^4, Ls=8 (1 core)"}
 
     if rank == 0:
         solve_ms = dt / args.steps * 1e3
@@ -503,7 +730,10 @@ def main():
                       "true_resid_5d": stats[0]["true_resid_5d"],
                       "fp64_plain": fp64,
                       "speedup_vs_fp64": (fp64["solve_ms"] / solve_ms) if fp64 else None},
-            "roofline": {"kernel": "D_bb apply (hop pass A + pass B, FP32)", "bound": "hbm",
+            "accuracy": accuracy,
+            "alu": alu,
+            "roofline": {"kernel": "D_bb apply inside the CG (pass A on B p, pass B; FP32)",
+                         "bound": "hbm",
                          "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
                          "peak_kind": peak_kind, "traffic": measured_traffic(),

@@ -68,3 +68,15 @@ def test_scan_iterations_match_oracle_cgnr():
     # the ratio the scan reports is the oracle's trend: alpha = 0.55 needs fewer iterations
     k1 = res["alphas"].index(1.0)
     assert res["ratio_mean"][res["alphas"].index(0.55)] < res["ratio_mean"][k1] == 1.0
+
+
+@pytest.mark.gpu
+def test_zolo_projection_mode_smoke():
+    """bench.py --zolo-projection on 4^4 (Zolotarev Ls = 4 against Mobius Ls = 16):
+    every solve converges and the reported factors are positive."""
+    import bench
+    out = bench.run_zolo_projection(None, lattice=(4, 4, 4, 4), ls_zolo=4, ls_mobius=16,
+                                    alphas=(0.5, 1.0))
+    for k in ("zolotarev_best_alpha", "zolotarev_alpha1", "mobius_alpha1"):
+        assert out[k]["true_resid"] <= 1e-8 and out[k]["iterations"] > 0
+    assert out["factor_time"] > 0 and out["factor_iterations_x_Ls"] > 0

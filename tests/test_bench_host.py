@@ -42,3 +42,18 @@ def test_clock_parsing():
     c = bench.parse_clock_samples(["0, 1400, 2070, 700, 0x8, Active, Not Active, Not Active, Not Active"])
     assert c["reasons"] == ["hw_slowdown"] and c["sm_mhz"] == 1400.0
     assert bench.parse_clock_samples([]) is None
+
+
+def test_sign_error_matches_zolotarev_ripple():
+    """The sign-approximation error used to match Ls in --zolo-projection equals the
+    equal-ripple maximum of the Zolotarev coefficients, and for constant a_i = 2
+    (Mobius b + c = 2) it is the closed form at the interval ends:
+    1 - R(x) = 2 q^L / (1 + q^L), q = |1 - 2x| / (1 + 2x)."""
+    import numpy as np
+    from synthetic import zolotarev_sign_coefficients
+    a, delta = zolotarev_sign_coefficients(8, 0.05, 6.0)
+    assert abs(bench.sign_error(a) - delta) < 1e-3 * delta
+    L = 16
+    q = [abs(1 - 2 * x) / (1 + 2 * x) for x in (0.05, 6.0)]
+    closed = max(2 * v ** L / (1 + v ** L) for v in q)
+    assert abs(bench.sign_error(np.full(L, 2.0)) - closed) < 1e-6 * closed
