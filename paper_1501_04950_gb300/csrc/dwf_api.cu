@@ -204,7 +204,8 @@ struct dwf_ctx {
   void* gauge[3] = {nullptr, nullptr, nullptr};  // FP64, FP32, FP16
   int* nbr = nullptr;                            // [2][Vh][8] neighbour table
   int* dev_err = nullptr;                        // set by a kernel whose bounded wait gave up
-  int use_tma = 0;                               // DWF_TMA: tensor-copy staged tuned kernels
+  int use_tma = 0;                               // tensor-copy staged tuned kernels (autotuned)
+  int env_tma = 0;                               // DWF_TMA set: staging fixed to tensor copies
   long long wait_budget = 0;                     // DWF_WAIT_BUDGET: clock cycles per bounded wait
   int skip_hop = -1;                             // DWF_TEST_SKIP_HOP: the first staged launch
                                                  // issues no copies for this hop (timeout test)
@@ -233,7 +234,12 @@ struct dwf_ctx {
   int* d_active = nullptr;         // per right-hand-side active mask of a batched solve
   int* pinned_i = nullptr;         // host staging of the mask
   int active_cap = 0;
-  std::map<std::string, std::pair<int, int>> tune;  // autotuned (rhs block, staging)
+  struct Tuned {
+    int nb, tma, tile;  // right-hand-side block, staging variant, 4D sites per CTA (0: default)
+  };
+  std::map<std::string, Tuned> tune;  // autotuned launch shapes
+  int tile = 0;                      // 4D sites per CTA of the tuned hop kernels (0: default)
+  int env_tile = -1;                 // DWF_HOP_TILE set: tile fixed (-1: autotuned)
 };
 
 namespace {
@@ -357,9 +363,11 @@ int get_ws(dwf_ctx* h, const std::string& name, size_t bytes, void** out) {
 }
 
 int ensure_reduce(dwf_ctx* h, int nrhs) {
-  const int need_blocks =
+  int need_blocks =
       std::max(hop_grid_blocks(h->g, P64, 0), std::max(hop_grid_blocks(h->g, P32, 0),
                                                        blas_grid_blocks(h->g)));
+  if (h->Ls == 8 || h->Ls == 12 || h->Ls == 16)  // the small tile of the tuned kernels
+    need_blocks = std::max(need_blocks, hop_grid_blocks(h->g, P32, hop2::small_block_sites(h->Ls)));
   if (h->scal && h->scal_rhs >= nrhs && h->partial_stride >= need_blocks) return DWF_OK;
   if (h->scal) {
     cudaFree(h->scal);
@@ -406,6 +414,7 @@ HopLaunch base_hop(dwf_ctx* h, int prec, int p, int nrhs, size_t stride) {
   L.nbr = h->nbr;
   L.err = h->dev_err;
   L.use_tma = h->use_tma;
+  L.block_sites = h->tile;
   L.wait_budget = h->wait_budget;
   L.skip_hop = &h->skip_hop;  // one-shot test hook, consumed by the first staged launch
   return L;
@@ -1183,48 +1192,59 @@ int solver_params(dwf_ctx* h, int* prec, double* delta, bool* restart) {
   return DWF_OK;
 }
 
-// Autotuner for the batched solve: times the batched D_bb apply of the inner
-// precision for every right-hand-side block size that fits in free device
-// memory, with direct and bulk-copy neighbour staging, and keeps the fastest
-// per right-hand side (within 3%, the larger block).  Results are cached per
-// (lattice, Ls, precision, nrhs) in the handle and, if DWF_AUTOTUNE_CACHE names
-// a file, there as "key nb staging" lines.
+// Autotuner of the launch shapes of the solver: times the (batched) D_bb apply
+// of the inner precision for every right-hand-side block size that fits in free
+// device memory (batched solves), every CTA tile of the tuned hop kernels
+// (default and small) and both neighbour staging variants (direct loads,
+// tensor-copy staging), and keeps the fastest per right-hand side (within 3%,
+// the larger block).  Results are cached per (lattice, Ls, precision, nrhs) in
+// the handle and, if DWF_AUTOTUNE_CACHE names a file, there as
+// "key nb staging tile" lines.  An explicit rhs_block option fixes the block;
+// DWF_TMA (set at dwf_create) fixes the staging.
 int choose_rhs_block(dwf_ctx* h, int nrhs, int prec, cudaStream_t st, int* nb_out) {
-  if (h->opt.rhs_block > 0) {
-    *nb_out = std::min(h->opt.rhs_block, nrhs);
-    return DWF_OK;
-  }
-  if (nrhs == 1) {
-    *nb_out = 1;
-    return DWF_OK;
+  const int Ls = h->g.Ls;
+  const bool tuned = !g_disable_tuned && (Ls == 8 || Ls == 12 || Ls == 16);
+  const bool fixed_nb = h->opt.rhs_block > 0 || nrhs == 1;
+  const int fnb = nrhs == 1 ? 1 : std::min(std::max(h->opt.rhs_block, 1), nrhs);
+  if (!tuned) {  // one generic kernel shape: only the block is tuned (or fixed)
+    if (fixed_nb) {
+      *nb_out = fnb;
+      return DWF_OK;
+    }
   }
   std::ostringstream key;
-  key << h->g.L[0] << "x" << h->g.L[1] << "x" << h->g.L[2] << "x" << h->g.L[3] << "_Ls" << h->g.Ls
-      << "_p" << prec << "_n" << nrhs;
+  key << "v2_" << h->g.L[0] << "x" << h->g.L[1] << "x" << h->g.L[2] << "x" << h->g.L[3] << "_Ls" << Ls
+      << "_p" << prec << "_n" << nrhs << "_b" << (fixed_nb ? fnb : 0) << "_t" << h->env_tma
+      << "_s" << h->env_tile;
   auto it = h->tune.find(key.str());
   const char* cache_file = std::getenv("DWF_AUTOTUNE_CACHE");
   if (it == h->tune.end() && cache_file) {
     std::ifstream in(cache_file);
     std::string k;
-    int nb, tma;
-    while (in >> k >> nb >> tma)
-      if (k == key.str()) h->tune[k] = std::make_pair(nb, tma);
+    int nb, tma, tile;
+    while (in >> k >> nb >> tma >> tile)
+      if (k == key.str()) h->tune[k] = dwf_ctx::Tuned{nb, tma, tile};
     it = h->tune.find(key.str());
   }
   if (it != h->tune.end()) {
-    *nb_out = std::min(it->second.first, nrhs);
-    h->use_tma = it->second.second;
+    *nb_out = std::min(it->second.nb, nrhs);
+    h->use_tma = it->second.tma;
+    h->tile = it->second.tile;
     return DWF_OK;
   }
-  size_t freeb = 0, totalb = 0;
-  CUCHK(h, cudaMemGetInfo(&freeb, &totalb));
-  const size_t per = solve_bytes_per_rhs(h->g, prec) + 3 * field_bytes(h->g, prec);
-  const double budget = 0.8 * (double)freeb;
-  const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
   std::vector<int> ok;
-  for (int c : cand)
-    if (c <= nrhs && (double)c * per <= budget) ok.push_back(c);
-  if (ok.empty()) ok.push_back(1);
+  if (fixed_nb) {
+    ok.push_back(fnb);
+  } else {
+    size_t freeb = 0, totalb = 0;
+    CUCHK(h, cudaMemGetInfo(&freeb, &totalb));
+    const size_t per = solve_bytes_per_rhs(h->g, prec) + 3 * field_bytes(h->g, prec);
+    const double budget = 0.8 * (double)freeb;
+    const int cand[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+    for (int c : cand)
+      if (c <= nrhs && (double)c * per <= budget) ok.push_back(c);
+    if (ok.empty()) ok.push_back(1);
+  }
   const int maxnb = ok.back();
   const size_t fi = field_bytes(h->g, prec);
   void *x, *y, *t;
@@ -1238,35 +1258,47 @@ int choose_rhs_block(dwf_ctx* h, int nrhs, int prec, cudaStream_t st, int* nb_ou
   cudaEvent_t e0, e1;
   CUCHK(h, cudaEventCreate(&e0));
   CUCHK(h, cudaEventCreate(&e1));
-  const int saved_tma = h->use_tma;
-  double best = 1e300;
-  int best_nb = 1, best_tma = saved_tma;
-  for (int nb : ok) {
-    for (int tma = 0; tma < 2; tma++) {
-      h->use_tma = tma;
-      if ((rc = apply_dbb(h, view_of(*ms), prec, y, x, t, nb, nullptr, st))) return rc;
-      CUCHK(h, cudaEventRecord(e0, st));
-      for (int k = 0; k < 3; k++)
-        if ((rc = apply_dbb(h, view_of(*ms), prec, y, x, t, nb, nullptr, st))) return rc;
-      CUCHK(h, cudaEventRecord(e1, st));
-      CUCHK(h, cudaEventSynchronize(e1));
-      float ms_t = 0.f;
-      CUCHK(h, cudaEventElapsedTime(&ms_t, e0, e1));
-      const double per_rhs = ms_t / (3.0 * nb);
-      if (per_rhs < 0.97 * best || (per_rhs <= best * 1.03 && nb > best_nb)) {
-        if (per_rhs < best) best = per_rhs;
-        best_nb = nb;
-        best_tma = tma;
-      }
-    }
+  std::vector<int> tmas = {h->env_tma};
+  std::vector<int> tiles = {h->env_tile >= 0 ? h->env_tile : 0};
+  if (tuned) {
+    if (!h->env_tma) tmas.push_back(1);
+    if (h->env_tile < 0) tiles.push_back(hop2::small_block_sites(Ls));
   }
+  double best = 1e300;
+  int best_nb = ok.front(), best_tma = tmas.front(), best_tile = 0;
+  const bool single = ok.size() == 1 && tmas.size() == 1 && (tiles.size() == 1 || tmas[0]);
+  best_tile = tiles.front();
+  if (!single)
+  for (int nb : ok)
+    for (int tma : tmas)
+      for (int tile : tiles) {
+        if (tma && tile) continue;  // the staged variant has one tile
+        h->use_tma = tma;
+        h->tile = tile;
+        if ((rc = apply_dbb(h, view_of(*ms), prec, y, x, t, nb, nullptr, st))) return rc;
+        CUCHK(h, cudaEventRecord(e0, st));
+        for (int k = 0; k < 3; k++)
+          if ((rc = apply_dbb(h, view_of(*ms), prec, y, x, t, nb, nullptr, st))) return rc;
+        CUCHK(h, cudaEventRecord(e1, st));
+        CUCHK(h, cudaEventSynchronize(e1));
+        float ms_t = 0.f;
+        CUCHK(h, cudaEventElapsedTime(&ms_t, e0, e1));
+        const double per_rhs = ms_t / (3.0 * nb);
+        if (per_rhs < 0.97 * best || (per_rhs <= best * 1.03 && nb > best_nb)) {
+          if (per_rhs < best) best = per_rhs;
+          best_nb = nb;
+          best_tma = tma;
+          best_tile = tile;
+        }
+      }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   h->use_tma = best_tma;
-  h->tune[key.str()] = std::make_pair(best_nb, best_tma);
+  h->tile = best_tile;
+  h->tune[key.str()] = dwf_ctx::Tuned{best_nb, best_tma, best_tile};
   if (cache_file) {
     std::ofstream out(cache_file, std::ios::app);
-    out << key.str() << " " << best_nb << " " << best_tma << "\n";
+    out << key.str() << " " << best_nb << " " << best_tma << " " << best_tile << "\n";
   }
   *nb_out = best_nb;
   return DWF_OK;
@@ -1338,6 +1370,13 @@ int dwf_create(dwf_handle* out, const int lattice[4], int Ls, double M5, double 
   // memory with tensor copies (measured slower than direct loads on the
   // 16^3x32 workload; kept as an alternative staging strategy).
   h->use_tma = std::getenv("DWF_TMA") != nullptr;
+  h->env_tma = h->use_tma;
+  // DWF_HOP_TILE=small|default fixes the CTA tile of the tuned hop kernels
+  if (const char* e = std::getenv("DWF_HOP_TILE")) {
+    const bool tuned_ls = Ls == 8 || Ls == 12 || Ls == 16;
+    h->env_tile = (std::string(e) == "small" && tuned_ls) ? hop2::small_block_sites(Ls) : 0;
+    h->tile = h->env_tile;
+  }
   h->bp_fused = std::getenv("DWF_NO_BP_FUSED") == nullptr;
   if (const char* e = std::getenv("DWF_WAIT_BUDGET")) h->wait_budget = std::atoll(e);
   if (const char* e = std::getenv("DWF_TEST_SKIP_HOP")) h->skip_hop = std::atoi(e);

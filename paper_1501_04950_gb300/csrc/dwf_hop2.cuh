@@ -592,8 +592,8 @@ __device__ __forceinline__ void epilogue_g(const Args<typename SP::T>& a, const 
 }
 
 // out = c_hop G post(H v') + c_loc loc(w), two 5th-dimension slices per thread.
-template <class SP, int LS, int PRE, int POST, int LOC, bool G5, bool NORM, int MINB>
-__global__ void __launch_bounds__(128, MINB) hop_kernel(const Geom g, const Args<typename SP::T> a) {
+template <class SP, int LS, int PRE, int POST, int LOC, bool G5, bool NORM, int MINB, int NT = 128>
+__global__ void __launch_bounds__(NT, MINB) hop_kernel(const Geom g, const Args<typename SP::T> a) {
   using T = typename SP::T;
   using V = typename Pr<T>::V;
   constexpr int SST = site_stride(LS);
@@ -703,7 +703,10 @@ __global__ void __launch_bounds__(128) local_kernel(const Geom g, void* out, con
 namespace dwf {
 namespace hop2 {
 
+// 4D sites per CTA: the default tile (128 threads) and the small one (64 threads);
+// HopLaunch.block_sites selects the small tile when it equals small_block_sites.
 inline int block_sites(int Ls) { return 128 / (Ls / 2); }
+inline int small_block_sites(int Ls) { return 64 / (Ls / 2); }
 
 inline size_t smem_bytes(int Ls, int S, size_t ts) {
   return ts * ((size_t)chain_block(Ls) + (size_t)S * site_stride(Ls));
@@ -788,20 +791,33 @@ cudaError_t run(const Geom& g, const HopLaunch& L, cudaStream_t st) {
   a.cstride = L.cstride;
   a.active = L.active;
   a.err = L.err;
-  const int S = block_sites(LS);
   if (L.use_tma) return run_tma<SP, LS, PRE, POST, LOC, G5, NORM>(g, L, a, st);
+  const bool small = L.block_sites == small_block_sites(LS);
+  const int S = small ? small_block_sites(LS) : block_sites(LS);
   dim3 block(LS / 2, S, 1);
   dim3 grid((g.Vh + S - 1) / S, 1, L.nrhs);
   const size_t smem = smem_bytes(LS, S, sizeof(T));
   constexpr int MB = min_blocks<T>();
-  auto k = hop_kernel<SP, LS, PRE, POST, LOC, G5, NORM, MB>;
-  static bool attr = false;  // dynamic shared memory limit, set once per kernel
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
+  // dynamic shared memory limits, set once per kernel
+  if (small) {
+    auto k = hop_kernel<SP, LS, PRE, POST, LOC, G5, NORM, 2 * MB, 64>;
+    static bool attr_small = false;
+    if (!attr_small) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr_small = true;
+    }
+    k<<<grid, block, smem, st>>>(g, a);
+  } else {
+    auto k = hop_kernel<SP, LS, PRE, POST, LOC, G5, NORM, MB>;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k<<<grid, block, smem, st>>>(g, a);
   }
-  k<<<grid, block, smem, st>>>(g, a);
   return cudaGetLastError();
 }
 

@@ -136,3 +136,30 @@ def test_staged_matches_direct_loads(Ls, prec, monkeypatch):
     monkeypatch.delenv("DWF_TMA", raising=False)
     for k in range(2):
         assert torch.equal(outs[0][k], outs[1][k])
+
+
+@pytest.mark.parametrize("Ls", [8, 12, 16])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_small_tile_matches_default_tile(Ls, prec, monkeypatch):
+    """The small CTA tile of the tuned hop kernels (DWF_HOP_TILE=small, 64 threads)
+    against the default tile: bitwise equal D_bb and D_bb^+ (ragged last CTAs for
+    Ls = 8 and 12)."""
+    sysm = make_case((6, 4, 2, 6), Ls, "varying", alpha=0.8, bc_t=-1, black=1)
+    psi = torch.from_numpy(gaussian_half5d(sysm.lattice, Ls, seed=11)).cuda()
+    outs = []
+    for tile in ("default", "small"):
+        monkeypatch.setenv("DWF_HOP_TILE", tile)
+        op = _op(sysm)
+        op.load_gauge(torch.from_numpy(sysm.U).cuda())
+        x = op.new_field(prec)
+        op.pack_half(x, psi, prec)
+        res = []
+        for fn in (op.apply_Dbb, op.apply_Dbb_dag):
+            y = op.new_field(prec)
+            fn(y, x, prec)
+            res.append(y.cpu())
+        outs.append(res)
+        op.close()
+    monkeypatch.delenv("DWF_HOP_TILE", raising=False)
+    for k in range(2):
+        assert torch.equal(outs[0][k], outs[1][k])
