@@ -630,7 +630,7 @@ bool is_device_ptr(const void* p) {
 struct SolveWork {
   void *b_hi, *x_hi, *r_hi, *t64, *t64r;  // FP64 black (t64r red)
   void *p, *r, *w, *z, *xlo, *tb, *tr;    // inner precision
-  void *p2, *bp;                          // second p buffer and B p (fused CG, FP32/FP64)
+  void *p2, *bp;                          // second p buffer and B p (fused CG)
 };
 
 int alloc_solve_work(dwf_ctx* h, int prec, SolveWork& W, int nb = 1) {
@@ -651,7 +651,7 @@ int alloc_solve_work(dwf_ctx* h, int prec, SolveWork& W, int nb = 1) {
   if ((rc = get_ws(h, "tb" + sfx, fi, &W.tb))) return rc;
   if ((rc = get_ws(h, "tr" + sfx, fi, &W.tr))) return rc;
   W.p2 = W.bp = nullptr;
-  if (prec == P32 || prec == P64) {
+  {
     if ((rc = get_ws(h, "p2" + sfx, fi, &W.p2))) return rc;
     if ((rc = get_ws(h, "bp" + sfx, fi, &W.bp))) return rc;
   }
@@ -661,7 +661,7 @@ int alloc_solve_work(dwf_ctx* h, int prec, SolveWork& W, int nb = 1) {
 // Bytes of solver workspace per right-hand side (used by the autotuner's memory check).
 size_t solve_bytes_per_rhs(const Geom& g, int prec) {
   const int xprec = (prec == P16 || prec == PB16) ? P32 : prec;
-  const int extra = (prec == P32 || prec == P64) ? 2 : 0;  // second p buffer, B p
+  const int extra = 2;  // second p buffer, B p
   return 5 * field_bytes(g, P64) + (6 + extra) * field_bytes(g, prec) + field_bytes(g, xprec);
 }
 
@@ -812,8 +812,10 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
   const bool fused = form == DWF_SCHUR_PRECOND && h->fused_cg && !g_disable_tuned &&
                      (Ls == 8 || Ls == 12 || Ls == 16);
   if (fused && (rc = apply_hat(h, cv, prec, W.tb, W.r, nb, s))) return rc;
-  // FP32 / FP64 inner fields: the p update also forms B p for D_bb pass A
-  const bool with_bp = fused && W.bp != nullptr && h->bp_fused;
+  // the p update also forms B p (of the stored p) for D_bb pass A; with BF16
+  // fields the rounding of B p to 8 significand bits costs more iterations than
+  // pass A saves (Zolotarev 24^3x48: 3288 against 2600), so BF16 folds B into pass A
+  const bool with_bp = fused && W.bp != nullptr && h->bp_fused && prec != PB16;
   if (with_bp) CUCHK(h, cudaMemsetAsync(W.p2, 0, fi * nb, s));
 
   auto enqueue_fused = [&](int cur, bool first) -> int {

@@ -334,21 +334,30 @@ __global__ void __launch_bounds__(kBlasThreads) pxb_update_kernel(
       SPX::store_pair(reinterpret_cast<char*>(x) + offx, m, NP, xv[0], xv[1]);
     }
     // p_new on the pair, v+ of the slice below and v- of the slice above
-    Spinor<T> q[2];
-    cplx<T> below[6], above[6];
+    Spinor<T> q[2], qb, qa;
 #pragma unroll
     for (int k = 0; k < 12; k++) {
 #pragma unroll
       for (int l = 0; l < 2; l++)
         q[l].c[k] = cmake(fma(beta, pv[l].c[k].re, zv[l].c[k].re), fma(beta, pv[l].c[k].im, zv[l].c[k].im));
-    }
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-      below[k] = cmake(fma(beta, pl[1].c[k].re, zl[1].c[k].re), fma(beta, pl[1].c[k].im, zl[1].c[k].im));
-      above[k] = cmake(fma(beta, pu[0].c[6 + k].re, zu[0].c[6 + k].re),
-                       fma(beta, pu[0].c[6 + k].im, zu[0].c[6 + k].im));
+      qb.c[k] = cmake(fma(beta, pl[1].c[k].re, zl[1].c[k].re), fma(beta, pl[1].c[k].im, zl[1].c[k].im));
+      qa.c[k] = cmake(fma(beta, pu[0].c[k].re, zu[0].c[k].re), fma(beta, pu[0].c[k].im, zu[0].c[k].im));
     }
     SP::store_pair(reinterpret_cast<char*>(pnew) + off, m, NP, q[0], q[1]);
+    if constexpr (SP::kScaled) {
+      // 16-bit storage: B acts on the stored (rounded) p_new, as pass B's local
+      // term sees it; the slices below and above round with their own scales
+      SP::quantize(q[0]);
+      SP::quantize(q[1]);
+      SP::quantize(qb);
+      SP::quantize(qa);
+    }
+    cplx<T> below[6], above[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      below[k] = qb.c[k];
+      above[k] = qa.c[6 + k];
+    }
     const int s0 = 2 * t;
     const T dp0 = bd[s0], dp1 = bd[s0 + 1], op0 = bo[s0], op1 = bo[s0 + 1];
     const T dm0 = bd[g.Ls + s0], dm1 = bd[g.Ls + s0 + 1], om0 = bo[g.Ls + s0], om1 = bo[g.Ls + s0 + 1];
@@ -657,6 +666,14 @@ cudaError_t launch_pxb_update(const Geom& g, int prec, int xprec, void* x, const
     pxb_update_kernel<Store64, Store64><<<grid, kBlasThreads, 0, s>>>(
         g, x, p, pnew, bp, z, a_ptr, num, den, sstride, sx, sp, reinterpret_cast<const double*>(bdiag),
         reinterpret_cast<const double*>(boff), cstride, active, do_x);
+  } else if (prec == P16 && xprec == P32) {
+    pxb_update_kernel<Store32, Store16<false>><<<grid, kBlasThreads, 0, s>>>(
+        g, x, p, pnew, bp, z, a_ptr, num, den, sstride, sx, sp, reinterpret_cast<const float*>(bdiag),
+        reinterpret_cast<const float*>(boff), cstride, active, do_x);
+  } else if (prec == PB16 && xprec == P32) {
+    pxb_update_kernel<Store32, Store16<true>><<<grid, kBlasThreads, 0, s>>>(
+        g, x, p, pnew, bp, z, a_ptr, num, den, sstride, sx, sp, reinterpret_cast<const float*>(bdiag),
+        reinterpret_cast<const float*>(boff), cstride, active, do_x);
   } else {
     return cudaErrorInvalidValue;
   }

@@ -153,7 +153,8 @@ cudaError_t launch_px_update(const Geom& g, int prec, int xprec, void* x, void* 
 // pnew = z + beta p (beta = num / den), bp = B pnew (B of Eq. mobius1 with D_w -> 1,
 // per right-hand side coefficients bdiag/boff [2][Ls] in prec's compute type with
 // stride cstride); with do_x also the deferred x += a_prev p.  p and pnew are
-// different buffers.  Ls even, prec FP32 (x FP32 or FP64) or FP64.
+// different buffers; 16-bit storage applies B to the stored (rounded) p_new.
+// Ls even; prec FP32 (x FP32 or FP64), FP64, or FP16/BF16 with x in FP32.
 cudaError_t launch_pxb_update(const Geom& g, int prec, int xprec, void* x, const void* p, void* pnew,
                               void* bp,
                               const void* z, const double* a_ptr, const double* num,
