@@ -374,8 +374,13 @@ def run_batched(args):
     from synthetic import gauge_field, point_source4d
     dev = torch.device("cuda", 0)
     out = []
-    for lat in args.batched.split(","):
-        L = tuple(int(v) for v in lat.split("x"))
+    lats = [tuple(int(v) for v in lat.split("x")) for lat in args.batched.split(",")]
+    # launch shapes tuned by the first solve of a lattice are reused by later handles
+    own_cache = "DWF_AUTOTUNE_CACHE" not in os.environ
+    if own_cache:
+        os.environ["DWF_AUTOTUNE_CACHE"] = os.path.join(
+            tempfile.gettempdir(), "dwf_bench_tune_%d.txt" % os.getpid())
+    for lat, L in zip(args.batched.split(","), lats):
         U = torch.from_numpy(gauge_field(L, EPS, seed=0)).to(dev)
         srcs = [point_source4d(L, sp, c) for sp in range(4) for c in range(3)]
         src = torch.from_numpy(np.stack(srcs + srcs)).to(dev)
@@ -402,7 +407,59 @@ def run_batched(args):
             op.close()
         out.append(row)
         print(json.dumps(row), flush=True)
+    if len(lats) > 1:
+        out.append(run_multi_lattice(lats, dev, 24))
+    # several small single-source problems, none of which fills the GPU alone
+    small = [(8, 8, 8, 8), (8, 8, 8, 16), (8, 8, 16, 16), (12, 12, 12, 12)]
+    out.append(run_multi_lattice(small, dev, 1))
+    if own_cache:
+        path = os.environ.pop("DWF_AUTOTUNE_CACHE")
+        if os.path.exists(path):
+            os.remove(path)
     return out
+
+
+def run_multi_lattice(lats, dev, nrhs):
+    """Point-source solves on several lattices (FP32 inner; nrhs sources each: the 12
+    spin-colour sources at alpha 1 and, for 24, again at alpha 1.5) solved one lattice
+    after another, then all in one dwf_cgne_solve_multi call (one host thread and stream
+    per lattice), on the same tuned handles."""
+    import torch
+    from paper_1501_04950_gb300 import dwf
+    from synthetic import gauge_field, point_source4d
+    ops, jobs = [], []
+    alphas = ([1.0] * 12 + [1.5] * 12)[:nrhs]
+    for L in lats:
+        U = torch.from_numpy(gauge_field(L, EPS, seed=0)).to(dev)
+        srcs = [point_source4d(L, sp, c) for sp in range(4) for c in range(3)]
+        src = torch.from_numpy(np.stack((srcs + srcs)[:nrhs])).to(dev)
+        op = dwf.DWF(L, LS, M5, MASS, 1.0, np.full(LS, B), np.full(LS, C))
+        op.load_gauge(U)
+        ops.append(op)
+        jobs.append((op, src, torch.empty_like(src), nrhs, alphas))
+    if nrhs == 1:  # first-use costs (launch-shape tuning, workspace) outside the timing
+        for op, src, prop, n, al in jobs:
+            op.cgne_solve(src, prop, nrhs=n, alphas=al, allow_not_converged=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for op, src, prop, n, al in jobs:
+        op.cgne_solve(src, prop, nrhs=n, alphas=al, allow_not_converged=True)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    st = dwf.cgne_solve_multi(jobs, allow_not_converged=True)
+    torch.cuda.synchronize()
+    t_multi = time.perf_counter() - t0
+    nsolve = nrhs * len(lats)
+    row = {"multi_lattice_one_call": {
+        "lattices": ["x".join(str(v) for v in L) for L in lats], "Ls": LS, "nrhs_each": nrhs,
+        "sequential_seconds": t_seq, "one_call_seconds": t_multi,
+        "solves_per_s_sequential": nsolve / t_seq, "solves_per_s_one_call": nsolve / t_multi,
+        "max_true_resid": max(x["true_resid"] for s in st for x in s)}}
+    for op in ops:
+        op.close()
+    print(json.dumps(row), flush=True)
+    return row
 
 
 def run_zolotarev(args):

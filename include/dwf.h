@@ -136,7 +136,8 @@ int dwf_default_options(dwf_options* opt);
 int dwf_create(dwf_handle* out, const int lattice[4], int Ls, double M5, double m,
                double alpha, const double* b, const double* c, const dwf_options* opt);
 int dwf_destroy(dwf_handle h);
-/* Message of the last failed call on h (or of the last failed dwf_create if h is NULL). */
+/* Message of the last failed call on h (or, if h is NULL, of the last failed
+ * dwf_create or dwf_cgne_solve_multi on the calling thread). */
 const char* dwf_last_error(dwf_handle h);
 
 /* Bytes of one internal half-field of precision prec (per right-hand side). */
@@ -216,6 +217,34 @@ int dwf_apply_dalpha(dwf_handle h, double* out_full, const double* in_full, doub
  * scalar is not finite or |D p|^2 <= 0. */
 int dwf_cgne_solve(dwf_handle h, const double* src4d, double* prop4d, double* sol5d, int nrhs,
                    const double* alphas, dwf_stats* stats, dwf_stream s);
+
+/* One lattice's propagator solve inside dwf_cgne_solve_multi: the arguments
+ * of dwf_cgne_solve for that handle, plus its own status (output). */
+typedef struct {
+  dwf_handle handle;    /* a distinct handle per job (its lattice, Ls, gauge, options) */
+  const double* src4d;  /* as in dwf_cgne_solve */
+  double* prop4d;
+  double* sol5d;
+  int nrhs;
+  const double* alphas;
+  dwf_stats* stats;
+  int status;           /* output: DWF_OK or the job's error code */
+} dwf_solve_job;
+
+/* Propagator solves of several lattices at once (Sec. 2 Eq. tosolve1, App. B
+ * Eq. tosolve, solved as in dwf_cgne_solve): every job runs the solve of
+ * dwf_cgne_solve on its own handle, one host thread per job, each on its
+ * handle's stream, so the kernels of small lattices, which alone fill only part
+ * of the GPU, overlap.  The paper has no counterpart: it is a batching of
+ * independent solves of Sec. 3's operator.
+ *   jobs   njobs entries; every handle distinct and created on the current device
+ *   s      the caller's stream: the jobs start once it has finished
+ * Returns DWF_OK when every job succeeded, else the status of the first failed
+ * job (jobs[i].status holds each job's own; dwf_last_error(jobs[i].handle) its
+ * message, dwf_last_error(NULL) the first failure's on this thread).  Two jobs
+ * with one handle are rejected (DWF_ERR_INVALID_ARG) before any work starts.
+ * Returns after every job has finished. */
+int dwf_cgne_solve_multi(dwf_solve_job* jobs, int njobs, dwf_stream s);
 
 /* The 4D overlap operator D_OV(m) = 1/2 [(1 + m) + (1 - m) gamma5 eps] of App. A
  * applied to nrhs 4D fields b, through the 5D system with the two masses of

@@ -21,7 +21,9 @@
 #include <limits>
 #include <sstream>
 #include <map>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/dwf.h"
@@ -1299,6 +1301,9 @@ int choose_rhs_block(dwf_ctx* h, int nrhs, int prec, cudaStream_t st, int* nb_ou
   h->tile = best_tile;
   h->tune[key.str()] = dwf_ctx::Tuned{best_nb, best_tma, best_tile};
   if (cache_file) {
+    // handles tuned on several host threads at once append whole lines
+    static std::mutex cache_mutex;
+    std::lock_guard<std::mutex> lock(cache_mutex);
     std::ofstream out(cache_file, std::ios::app);
     out << key.str() << " " << best_nb << " " << best_tma << " " << best_tile << "\n";
   }
@@ -1642,6 +1647,58 @@ int dwf_apply_overlap(dwf_handle h, const double* src4d, double* out4d, double* 
                       const double* alphas, dwf_stats* stats, dwf_stream s) {
   if (!h) return fail(h, DWF_ERR_INVALID_ARG, "bad argument");
   return solve_5d(h, src4d, out4d, sol5d, nrhs, alphas, stats, s, 1.0, h->m);
+}
+
+int dwf_cgne_solve_multi(dwf_solve_job* jobs, int njobs, dwf_stream s) {
+  // failures before any job starts: reported on the job's handle and on this thread
+  auto reject = [](dwf_ctx* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    g_create_error = msg;
+    return code;
+  };
+  if (!jobs || njobs < 1) return reject(nullptr, DWF_ERR_INVALID_ARG, "bad argument");
+  for (int i = 0; i < njobs; i++) {
+    if (!jobs[i].handle) return reject(nullptr, DWF_ERR_INVALID_ARG, "job without a handle");
+    for (int j = 0; j < i; j++)
+      if (jobs[j].handle == jobs[i].handle)
+        return reject(jobs[i].handle, DWF_ERR_INVALID_ARG,
+                      "two jobs of one dwf_cgne_solve_multi call share a handle");
+  }
+  for (int i = 0; i < njobs; i++) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != jobs[i].handle->device)
+      return reject(jobs[i].handle, DWF_ERR_INVALID_ARG, "handle created on another device");
+  }
+  // the jobs start after the caller's stream; each then runs on its handle's stream
+  {
+    cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(s));
+    if (e != cudaSuccess) return reject(jobs[0].handle, DWF_ERR_CUDA, cudaGetErrorString(e));
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto run = [&](int i) {
+    dwf_solve_job& J = jobs[i];
+    if (cudaSetDevice(dev) != cudaSuccess) {
+      J.status = fail(J.handle, DWF_ERR_CUDA, "cudaSetDevice failed on a worker thread");
+      return;
+    }
+    J.status = solve_5d(J.handle, J.src4d, J.prop4d, J.sol5d, J.nrhs, J.alphas, J.stats,
+                        reinterpret_cast<dwf_stream>(J.handle->cstream), J.handle->m, 1.0);
+  };
+  std::vector<std::thread> pool;
+  pool.reserve(njobs - 1);
+  for (int i = 1; i < njobs; i++) pool.emplace_back(run, i);
+  run(0);
+  for (auto& t : pool) t.join();
+  int rc = DWF_OK;
+  for (int i = 0; i < njobs && rc == DWF_OK; i++) rc = jobs[i].status;
+  if (rc != DWF_OK)
+    for (int i = 0; i < njobs; i++)
+      if (jobs[i].status != DWF_OK) {
+        g_create_error = "job " + std::to_string(i) + ": " + jobs[i].handle->err;
+        break;
+      }
+  return rc;
 }
 
 static int solve_5d(dwf_ctx* h, const double* src4d, double* prop4d, double* sol5d, int nrhs,

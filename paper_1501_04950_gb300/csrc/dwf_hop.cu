@@ -379,11 +379,14 @@ cudaError_t launch_hop(const Geom& g, const HopLaunch& L, cudaStream_t st) {
     }
     if (e != cudaErrorNotSupported) return e;
   }
-  switch (L.prec) {
-    case P64: return dispatch_hop<Store64>(g, L, st);
-    case P32: return dispatch_hop<Store32>(g, L, st);
-    case P16: return dispatch_hop<Store16<false>>(g, L, st);
-    case PB16: return dispatch_hop<Store16<true>>(g, L, st);
+  // block_sites is the tuned kernels' tile: the generic kernel takes its own default
+  HopLaunch G = L;
+  G.block_sites = 0;
+  switch (G.prec) {
+    case P64: return dispatch_hop<Store64>(g, G, st);
+    case P32: return dispatch_hop<Store32>(g, G, st);
+    case P16: return dispatch_hop<Store16<false>>(g, G, st);
+    case PB16: return dispatch_hop<Store16<true>>(g, G, st);
   }
   return cudaErrorInvalidValue;
 }

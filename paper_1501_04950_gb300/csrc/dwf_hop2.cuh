@@ -23,6 +23,7 @@
 //     for the unknown first element and one back-substitution sweep.
 #pragma once
 
+#include <atomic>
 #include <cstdlib>
 
 #include <cudaTypedefs.h>
@@ -712,6 +713,16 @@ inline size_t smem_bytes(int Ls, int S, size_t ts) {
   return ts * ((size_t)chain_block(Ls) + (size_t)S * site_stride(Ls));
 }
 
+// Raises a kernel's dynamic shared-memory limit once per process; safe when
+// several host threads launch through different handles at the same time.
+template <class K>
+cudaError_t smem_limit_once(K k, size_t smem, std::atomic<bool>& done) {
+  if (done.load(std::memory_order_acquire)) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done.store(true, std::memory_order_release);
+  return e;
+}
+
 // Tensor map of a half-field (nrhs fields back to back) as 32-bit words:
 // dim 0 the slice pairs of one row (component or 16-byte chunk row), dim 1 the
 // rows, dim 2 the right-hand sides; the box is one site (Ls/2 pairs) x all rows.
@@ -719,7 +730,8 @@ template <class SP, int LS>
 cudaError_t encode_field_map(CUtensorMap* map, const Geom& g, const void* base, size_t stride,
                              int nrhs) {
   using ST = Stage<SP, LS>;
-  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  static std::atomic<PFN_cuTensorMapEncodeTiled_v12000> enc_fn{nullptr};
+  PFN_cuTensorMapEncodeTiled_v12000 enc = enc_fn.load(std::memory_order_acquire);
   if (!enc) {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
@@ -727,6 +739,7 @@ cudaError_t encode_field_map(CUtensorMap* map, const Geom& g, const void* base, 
                                                      cudaEnableDefault, &q);
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    enc_fn.store(enc, std::memory_order_release);
   }
   const size_t NP = (size_t)g.N5 / 2;
   const cuuint64_t dims[3] = {(cuuint64_t)NP * ST::kWpp, (cuuint64_t)ST::kRows, (cuuint64_t)nrhs};
@@ -753,12 +766,9 @@ cudaError_t run_tma(const Geom& g, const HopLaunch& L, const Args<typename SP::T
   if (e != cudaSuccess) return e;
   const size_t smem = tma_smem_bytes<SP, LS, NST>();
   auto k = hop_tma_kernel<SP, LS, PRE, POST, LOC, G5, NORM, NST, 1>;
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<bool> attr{false};
+  e = smem_limit_once(k, smem, attr);
+  if (e != cudaSuccess) return e;
   dim3 grid((g.Vh + S - 1) / S, 1, L.nrhs);
   int skip = -1;
   if (L.skip_hop && *L.skip_hop >= 0) {
@@ -801,21 +811,15 @@ cudaError_t run(const Geom& g, const HopLaunch& L, cudaStream_t st) {
   // dynamic shared memory limits, set once per kernel
   if (small) {
     auto k = hop_kernel<SP, LS, PRE, POST, LOC, G5, NORM, 2 * MB, 64>;
-    static bool attr_small = false;
-    if (!attr_small) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr_small = true;
-    }
+    static std::atomic<bool> attr_small{false};
+    cudaError_t e = smem_limit_once(k, smem, attr_small);
+    if (e != cudaSuccess) return e;
     k<<<grid, block, smem, st>>>(g, a);
   } else {
     auto k = hop_kernel<SP, LS, PRE, POST, LOC, G5, NORM, MB>;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    static std::atomic<bool> attr{false};
+    cudaError_t e = smem_limit_once(k, smem, attr);
+    if (e != cudaSuccess) return e;
     k<<<grid, block, smem, st>>>(g, a);
   }
   return cudaGetLastError();
@@ -848,12 +852,9 @@ cudaError_t run_local(const Geom& g, const LocalLaunch& L, cudaStream_t st) {
   const int S = block_sites(LS);
   const size_t smem = smem_bytes(LS, S, sizeof(T));
   auto k = local_kernel<SP, LS, PROG>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<bool> attr{false};
+  cudaError_t e = smem_limit_once(k, smem, attr);
+  if (e != cudaSuccess) return e;
   Reduce red{};
   if (L.red) red = *L.red;
   dim3 block(LS / 2, S, 1);
@@ -954,12 +955,9 @@ cudaError_t run_rupdate(const Geom& g, const RUpdateLaunch& L, cudaStream_t st) 
   const int S = block_sites(LS);
   const size_t smem = smem_bytes(LS, S, sizeof(T));
   auto k = rupdate_kernel<SP, LS>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<bool> attr{false};
+  cudaError_t e = smem_limit_once(k, smem, attr);
+  if (e != cudaSuccess) return e;
   dim3 block(LS / 2, S, 1);
   dim3 grid((g.Vh + S - 1) / S, 1, L.nrhs);
   k<<<grid, block, smem, st>>>(g, L.r, L.rhat, L.w, L.stride, reinterpret_cast<const T*>(L.chain),

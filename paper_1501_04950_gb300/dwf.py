@@ -47,11 +47,18 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class SolveJobC(ctypes.Structure):
+    _fields_ = [("handle", ctypes.c_void_p), ("src4d", ctypes.c_void_p),
+                ("prop4d", ctypes.c_void_p), ("sol5d", ctypes.c_void_p), ("nrhs", ctypes.c_int),
+                ("alphas", ctypes.POINTER(ctypes.c_double)), ("stats", ctypes.POINTER(Stats)),
+                ("status", ctypes.c_int)]
+
+
 EXPORTS = [
     "dwf_default_options", "dwf_create", "dwf_destroy", "dwf_last_error", "dwf_field_bytes",
     "dwf_load_gauge", "dwf_pack_half", "dwf_unpack_half", "dwf_apply_Dbb", "dwf_apply_Dbb_dag",
     "dwf_apply_dalpha", "dwf_cgne_solve", "dwf_solve_normal", "dwf_force",
-    "dwf_apply_Dbb_noalloc", "dwf_apply_overlap", "dwf_action",
+    "dwf_apply_Dbb_noalloc", "dwf_apply_overlap", "dwf_action", "dwf_cgne_solve_multi",
 ]
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -80,6 +87,7 @@ def load_library(path: str = LIB_PATH):
         "dwf_solve_normal": (I, [P, P, P, ctypes.POINTER(Stats), P]),
         "dwf_force": (I, [P, P, P, P, I, P]),
         "dwf_action": (I, [P, ctypes.POINTER(D), P, P, ctypes.POINTER(Stats), P]),
+        "dwf_cgne_solve_multi": (I, [ctypes.POINTER(SolveJobC), I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -229,3 +237,37 @@ class DWF:
     def force(self, dSdU, phi_half, X_half=None, projected=False):
         self._check(self.lib.dwf_force(self.h, _ptr(dSdU), _ptr(phi_half), _ptr(X_half),
                                        int(bool(projected)), _stream()))
+
+
+def cgne_solve_multi(jobs, allow_not_converged=False):
+    """Propagator solves of several lattices in one call (dwf_cgne_solve_multi).
+
+    jobs: sequence of (op, src4d, prop4d[, nrhs[, alphas[, sol5d]]]) with a
+    distinct DWF handle per job (arguments as in DWF.cgne_solve).  Returns one list of stats dicts per job;
+    raises DWFError with the first failed job's status and message."""
+    n = len(jobs)
+    arr = (SolveJobC * n)()
+    keep = []
+    for i, job in enumerate(jobs):
+        op, src, prop = job[:3]
+        nrhs = int(job[3]) if len(job) > 3 else 1
+        alphas = job[4] if len(job) > 4 else None
+        sol = job[5] if len(job) > 5 else None
+        st = (Stats * nrhs)()
+        al = None
+        if alphas is not None:
+            al = (ctypes.c_double * nrhs)(*[float(a) for a in alphas])
+        keep.append((st, al))
+        arr[i].handle = op.h
+        arr[i].src4d = src.data_ptr()
+        arr[i].prop4d = prop.data_ptr()
+        arr[i].sol5d = sol.data_ptr() if sol is not None else None
+        arr[i].nrhs = nrhs
+        arr[i].alphas = al
+        arr[i].stats = st
+        arr[i].status = -1
+    L = lib()
+    rc = L.dwf_cgne_solve_multi(arr, n, _stream())
+    if rc != DWF_OK and not (allow_not_converged and rc == DWF_ERR_NOT_CONVERGED):
+        raise DWFError(rc, L.dwf_last_error(None).decode())
+    return [[s.as_dict() for s in keep[i][0]] for i in range(n)]
