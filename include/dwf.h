@@ -100,7 +100,11 @@ typedef struct {
   double rel_tol;        /* target |r'_b - D_bb x| / |r'_b| (default 1e-10)          */
   int maxiter;           /* total inner iterations per right-hand side (default 100000) */
   double reliable_delta; /* reliable update when |r| < delta * max|r|; <= 0 (default):
-                            0.5 for FP16/BF16 inner fields, 0.1 otherwise             */
+                            0.5 for FP16/BF16 inner fields, 0.1 otherwise.  With FP16/BF16
+                            inner fields (operator DWF_SCHUR_PRECOND) a replacement recomputes
+                            the residual in FP32 from the last FP64 one, r = r_64 - D x_32
+                            (x_32: the solution accumulated since), until |r| has dropped
+                            1e3-fold below |r_64| or reaches rel_tol; then in FP64      */
   int solver;            /* DWF_SOLVER_* (default DWF_SOLVER_RELIABLE)               */
   int check_every;       /* iterations between convergence polls; <= 0 (default): 4 for
                             FP16/BF16 inner fields, 16 otherwise                       */
@@ -112,7 +116,7 @@ typedef struct {
 
 typedef struct {
   int iterations;        /* CG iterations (inner, all restarts)                       */
-  int restarts;          /* reliable updates / defect-correction cycles               */
+  int restarts;          /* FP64 reliable updates / defect-correction cycles          */
   double true_resid;     /* FP64 |r'_b - D_bb x| / |r'_b| of the returned solution     */
   double true_resid_5d;  /* FP64 |rhs - D_alpha psi| / |rhs| of the full 5D solution    */
   double seconds;        /* wall time from the start of the batch's CG to this source's
@@ -123,6 +127,8 @@ typedef struct {
   int kernel_launches;   /* CUDA kernels the solve launched                             */
   double apply_ms;       /* device time of the batch's inner D_bb applies (opt.profile = 1) */
   double apply_dag_ms;   /* same for the D_bb^+ applies                                  */
+  int applies_fp32;      /* FP32 D_bb applies: residual replacements of FP16/BF16 solves
+                            between two FP64 ones                                       */
 } dwf_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -242,6 +242,8 @@ struct dwf_ctx {
   std::map<std::string, Tuned> tune;  // autotuned launch shapes
   int tile = 0;                      // 4D sites per CTA of the tuned hop kernels (0: default)
   int env_tile = -1;                 // DWF_HOP_TILE set: tile fixed (-1: autotuned)
+  double tier_eta = 1e-3;            // 16-bit solves: FP64 replacement once |r| < eta |r_64|
+                                     // (DWF_TIER_ETA; <= 0: every replacement in FP64)
 };
 
 namespace {
@@ -752,6 +754,10 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
   h->next_event = 0;
   std::vector<int> act(nb, 1), conv(nb, 0), its(nb, 0), rst(nb, 0), stalled(nb, 0), code(nb, 0);
   std::vector<double> bnorm(nb), rmax(nb), true_res(nb, 1.0), best(nb, 1.0), t_done(nb, -1.0);
+  // two-tier replacement (16-bit inner fields): |r_64| of the last FP64 replacement,
+  // best FP32-tier residual since, escalation flag, FP32 replacements
+  std::vector<double> anchor(nb, 0.0), best32(nb, 0.0);
+  std::vector<int> esc(nb, 0), n32(nb, 0);
   const auto t_start = std::chrono::steady_clock::now();
   auto now_s = [&]() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
@@ -799,6 +805,7 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
     const double bb = h->pinned[(size_t)r * kScal + S_BB];
     bnorm[r] = std::sqrt(bb);
     rmax[r] = bnorm[r];
+    anchor[r] = best32[r] = bnorm[r];
     if (!(bb > 0.0)) {
       act[r] = 0;
       if (bb == 0.0) {
@@ -818,6 +825,11 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
   // fields the rounding of B p to 8 significand bits costs more iterations than
   // pass A saves (Zolotarev 24^3x48: 3288 against 2600), so BF16 folds B into pass A
   const bool with_bp = fused && W.bp != nullptr && h->bp_fused && prec != PB16;
+  // Two-tier residual replacement for 16-bit inner fields: between FP64
+  // replacements r = r_64 - D x_lo in FP32, where r_64 is the FP64 residual of the
+  // last FP64 replacement and x_lo (FP32) the solution accumulated since; its
+  // error is ~1e-6 |r_64|, small against |r| while |r| > tier_eta |r_64|.
+  const bool tiered = (prec == P16 || prec == PB16) && form == DWF_SCHUR_PRECOND && h->tier_eta > 0;
   if (with_bp) CUCHK(h, cudaMemsetAsync(W.p2, 0, fi * nb, s));
 
   auto enqueue_fused = [&](int cur, bool first) -> int {
@@ -959,8 +971,8 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
       cleanup();
       return rc;
     }
-    bool update = false, changed = false;
-    std::vector<int> upd(nb, 0);
+    bool update = false, update32 = false, changed = false;
+    std::vector<int> upd(nb, 0), upd32(nb, 0);
     for (int r = 0; r < nb; r++) {
       if (!act[r]) continue;
       const double rr = h->pinned[(size_t)r * kScal + S_RR], ww = h->pinned[(size_t)r * kScal + S_WW];
@@ -972,9 +984,55 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
       }
       const double rn = std::sqrt(rr);
       if (rn < delta * rmax[r] || rn <= tol * bnorm[r] || it >= maxiter) {
-        upd[r] = 1;
-        update = true;
+        if (tiered && !esc[r] && rn > h->tier_eta * anchor[r] && rn > tol * bnorm[r] &&
+            it < maxiter) {
+          upd32[r] = 1;
+          update32 = true;
+        } else {
+          upd[r] = 1;
+          update = true;
+        }
       }
+    }
+    if (update32) {
+      // FP32-tier replacement: r = r_64 - D x_lo (x_lo keeps accumulating)
+      if ((rc = push_mask(upd32)) ||
+          (rc = apply_dbb(h, cv, P32, W.t64, W.xlo, W.t64r, nb, nullptr, s))) {
+        cleanup();
+        return rc;
+      }
+      KLAUNCH(h, launch_sub_to(h->g, prec, W.r, W.r_hi, W.t64, nb, fi, f64, fx, &red_rr, s,
+                               h->d_active));
+      if (fused && (rc = apply_hat(h, cv, prec, W.tb, W.r, nb, s))) {
+        cleanup();
+        return rc;
+      }
+      if ((rc = sync_read(h, nb, s))) {
+        cleanup();
+        return rc;
+      }
+      std::vector<int> restarted(nb, 0);
+      for (int r = 0; r < nb; r++) {
+        if (!upd32[r]) continue;
+        const double rn = std::sqrt(h->pinned[(size_t)r * kScal + S_RR]);
+        n32[r]++;
+        if (!std::isfinite(rn)) {
+          act[r] = 0;
+          code[r] = DWF_ERR_BREAKDOWN;
+          continue;
+        }
+        rmax[r] = rn;
+        // no 10% gain over the best FP32-tier residual: the next replacement is FP64
+        if (rn < 0.9 * best32[r]) best32[r] = rn;
+        else esc[r] = 1;
+        if (restart) restarted[r] = 1;
+      }
+      if (std::any_of(restarted.begin(), restarted.end(), [](int v) { return v != 0; }) &&
+          (rc = reset_beta(restarted))) {
+        cleanup();
+        return rc;
+      }
+      changed = true;
     }
     if (changed && !update && (rc = push_active())) {
       cleanup();
@@ -1014,6 +1072,8 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
         const double rrh = h->pinned[(size_t)r * kScal + S_RRHI];
         true_res[r] = std::sqrt(rrh) / bnorm[r];
         rmax[r] = std::sqrt(rrh);
+        anchor[r] = best32[r] = rmax[r];
+        esc[r] = 0;
         rst[r]++;
         if (true_res[r] <= tol) {
           conv[r] = 1;
@@ -1062,6 +1122,7 @@ int cgnr_batched(dwf_ctx* h, const CoefView& cv_in, int prec, double tol, int ma
       st[r].applies = its[r];
       st[r].applies_dag = its[r];
       st[r].applies_fp64 = rst[r];
+      st[r].applies_fp32 = n32[r];
       st[r].apply_ms = h->timed_ms[0];
       st[r].apply_dag_ms = h->timed_ms[1];
       st[r].kernel_launches = (int)(h->launches - launches0);
@@ -1385,6 +1446,7 @@ int dwf_create(dwf_handle* out, const int lattice[4], int Ls, double M5, double 
     h->tile = h->env_tile;
   }
   h->bp_fused = std::getenv("DWF_NO_BP_FUSED") == nullptr;
+  if (const char* e = std::getenv("DWF_TIER_ETA")) h->tier_eta = std::atof(e);
   if (const char* e = std::getenv("DWF_WAIT_BUDGET")) h->wait_budget = std::atoll(e);
   if (const char* e = std::getenv("DWF_TEST_SKIP_HOP")) h->skip_hop = std::atoi(e);
   h->fused_cg = std::getenv("DWF_UNFUSED_CG") == nullptr;

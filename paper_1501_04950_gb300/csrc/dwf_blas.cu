@@ -453,6 +453,39 @@ __global__ void __launch_bounds__(kBlasThreads) sub64_norm_kernel(
   block_sum_to(acc, red, rhs, gridDim.x, blockIdx.x);
 }
 
+// dst <- a - b with a FP64 and b FP32 (the difference in FP64), stored in the
+// precision of SPD; |dst|^2 of the stored values.
+template <class SPD>
+__global__ void __launch_bounds__(kBlasThreads) sub_to_kernel(
+    const Geom g, void* dst, const void* a, const void* b, size_t sd, size_t sa, size_t sb,
+    Reduce red, const int* active) {
+  using TD = typename SPD::T;
+  const int rhs = blockIdx.y;
+  if (active && !active[rhs]) return;
+  const int NP = g.N5 >> 1;
+  double acc = 0.0;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < NP; m += gridDim.x * blockDim.x) {
+    Spinor<double> x[2];
+    Spinor<float> y[2];
+    Store64::load_pair(reinterpret_cast<const char*>(a) + rhs * sa, m, NP, x[0], x[1]);
+    Store32::load_pair(reinterpret_cast<const char*>(b) + rhs * sb, m, NP, y[0], y[1]);
+    Spinor<TD> d[2];
+#pragma unroll
+    for (int l = 0; l < 2; l++)
+#pragma unroll
+      for (int k = 0; k < 12; k++)
+        d[l].c[k] = cmake<TD>((TD)(x[l].c[k].re - (double)y[l].c[k].re),
+                              (TD)(x[l].c[k].im - (double)y[l].c[k].im));
+    SPD::store_pair(reinterpret_cast<char*>(dst) + rhs * sd, m, NP, d[0], d[1]);
+    if constexpr (SPD::kScaled) {
+      SPD::quantize(d[0]);
+      SPD::quantize(d[1]);
+    }
+    acc += sqd(d[0]) + sqd(d[1]);
+  }
+  block_sum_to(acc, red, rhs, gridDim.x, blockIdx.x);
+}
+
 template <class SP>
 __global__ void __launch_bounds__(kBlasThreads) norm_kernel(const Geom g, const void* x,
                                                              size_t stride, Reduce red) {
@@ -691,6 +724,27 @@ cudaError_t launch_sub64_norm(const Geom& g, void* out, const void* a, const voi
                               size_t stride, const Reduce* red, cudaStream_t s, const int* active) {
   dim3 grid(elementwise_blocks((size_t)g.N5 / 2), nrhs);
   sub64_norm_kernel<<<grid, kBlasThreads, 0, s>>>(g, out, a, b, stride, *red, active);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub_to(const Geom& g, int prec_d, void* dst, const void* a64, const void* b32,
+                          int nrhs, size_t sd, size_t sa, size_t sb, const Reduce* red,
+                          cudaStream_t s, const int* active) {
+  dim3 grid(elementwise_blocks((size_t)g.N5 / 2), nrhs);
+  switch (prec_d) {
+    case P32:
+      sub_to_kernel<Store32><<<grid, kBlasThreads, 0, s>>>(g, dst, a64, b32, sd, sa, sb, *red, active);
+      break;
+    case P16:
+      sub_to_kernel<Store16<false>><<<grid, kBlasThreads, 0, s>>>(g, dst, a64, b32, sd, sa, sb, *red,
+                                                                  active);
+      break;
+    case PB16:
+      sub_to_kernel<Store16<true>><<<grid, kBlasThreads, 0, s>>>(g, dst, a64, b32, sd, sa, sb, *red,
+                                                                 active);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

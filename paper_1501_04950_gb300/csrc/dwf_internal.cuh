@@ -214,6 +214,10 @@ cudaError_t launch_accumulate64(const Geom& g, void* x64, int prec_s, void* src,
 cudaError_t launch_sub64_norm(const Geom& g, void* out, const void* a, const void* b, int nrhs,
                               size_t stride, const Reduce* red, cudaStream_t s,
                               const int* active = nullptr);
+// dst (prec_d: FP32, FP16 or BF16) = a (FP64) - b (FP32), |dst|^2 of the stored values -> red.
+cudaError_t launch_sub_to(const Geom& g, int prec_d, void* dst, const void* a64, const void* b32,
+                          int nrhs, size_t stride_d, size_t stride_a, size_t stride_b,
+                          const Reduce* red, cudaStream_t s, const int* active = nullptr);
 // |x|^2 -> red.
 cudaError_t launch_norm(const Geom& g, int prec, const void* x, int nrhs, size_t stride,
                         const Reduce* red, cudaStream_t s);

@@ -149,6 +149,35 @@ def test_batched_mixed_alpha_16bit(prec):
         assert np.abs(p[k] - p[k + 6]).max() / np.abs(p[k]).max() < 1e-7
 
 
+@pytest.mark.parametrize("prec,solver", [(2, 0), (3, 1)])
+def test_two_tier_replacement(prec, solver, monkeypatch):
+    """16-bit inner fields: residual replacements in FP32 between FP64 ones
+    (default) against FP64 at every replacement (DWF_TIER_ETA=0).  Both reach the
+    FP64 true residual 1e-10 and the oracle's z_1; the two-tier solve needs far
+    fewer FP64 applies."""
+    L = (8, 8, 4, 8)
+    src = gaussian_source4d(L, seed=7)
+    sysm = make_case(L, 8, "mobius", alpha=1.2, m=0.02, eps=0.3)
+    ref = O.solve_propagator(sysm, src, tol=1e-12)
+    res = {}
+    for eta in ("0", None):
+        if eta is None:
+            monkeypatch.delenv("DWF_TIER_ETA", raising=False)
+        else:
+            monkeypatch.setenv("DWF_TIER_ETA", eta)
+        prop, _, st = _solve(sysm, src, precision_inner=prec, solver=solver, maxiter=20000)
+        s = st[0]
+        err = np.abs(prop - ref["z1"]).max() / np.abs(ref["z1"]).max()
+        print("prec %d eta %s: iters %d fp64 %d fp32 %d resid %.2e z1 err %.2e"
+              % (prec, eta, s["iterations"], s["applies_fp64"], s["applies_fp32"],
+                 s["true_resid"], err))
+        assert s["true_resid"] <= 1e-10 and err < 1e-7
+        res[eta] = s
+    assert res["0"]["applies_fp32"] == 0
+    assert res[None]["applies_fp32"] > 0
+    assert res[None]["applies_fp64"] * 2 < res["0"]["applies_fp64"]
+
+
 @pytest.mark.parametrize("form", [1, 2])
 def test_schur_forms(form):
     """Eq. redblack1 (form 1) and its row-scaled form (form 2), Sec. 3: the
