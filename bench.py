@@ -582,6 +582,8 @@ def main():
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sweep", action="store_true", help="skip the alpha sweep")
+    ap.add_argument("--no-fp16", action="store_true",
+                    help="skip the FP16-inner solve of the workload after the timed region")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the sampled-site accuracy checks after the timed region")
     ap.add_argument("--apply-only", type=int, default=0,
@@ -718,6 +720,28 @@ def main():
                 "true_resid": s64["true_resid"]}
         op64.close()
 
+    # the same workload with FP16 inner fields (FP64 and FP32-tier residual
+    # replacements), outside the timed region: one warm-up solve, then two timed
+    inner16 = None
+    if rank == 0 and inner == dwf.FP32 and not args.no_fp16:
+        op16 = dwf.DWF(LATTICE, LS, M5, MASS, args.alpha, np.full(LS, B), np.full(LS, C),
+                       precision_inner=dwf.FP16)
+        op16.load_gauge(U)
+        prop16 = torch.empty_like(src)
+        op16.cgne_solve(src, prop16)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s16 = [op16.cgne_solve(src, prop16)[0] for _ in range(2)][-1]
+        f1.record(stream)
+        torch.cuda.synchronize()
+        inner16 = {"time_to_1e-10_ms": f0.elapsed_time(f1) / 2, "iterations": s16["iterations"],
+                   "fp64_replacements": s16["restarts"], "fp32_replacements": s16["applies_fp32"],
+                   "true_resid": s16["true_resid"],
+                   "z1_rel_diff_vs_fp32": float((prop16 - prop).abs().max() / prop.abs().max())}
+        op16.close()
+
     # accuracy of the timed workload's solution (outside the timed region): one
     # more solve with the full 5D solution, checked at sampled sites
     accuracy = None
@@ -788,7 +812,8 @@ def main():
                       "reliable_updates": stats[0]["restarts"], "true_resid": stats[0]["true_resid"],
                       "true_resid_5d": stats[0]["true_resid_5d"],
                       "fp64_plain": fp64,
-                      "speedup_vs_fp64": (fp64["solve_ms"] / solve_ms) if fp64 else None},
+                      "speedup_vs_fp64": (fp64["solve_ms"] / solve_ms) if fp64 else None,
+                      "fp16_inner": inner16},
             "accuracy": accuracy,
             "alu": alu,
             "roofline": {"kernel": "D_bb apply inside the CG (pass A on B p, pass B; FP32)",

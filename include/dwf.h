@@ -100,7 +100,7 @@ typedef struct {
   double rel_tol;        /* target |r'_b - D_bb x| / |r'_b| (default 1e-10)          */
   int maxiter;           /* total inner iterations per right-hand side (default 100000) */
   double reliable_delta; /* reliable update when |r| < delta * max|r|; <= 0 (default):
-                            0.5 for FP16/BF16 inner fields, 0.1 otherwise.  With FP16/BF16
+                            0.5 for FP16/BF16 inner fields, 0.01 otherwise.  With FP16/BF16
                             inner fields (operator DWF_SCHUR_PRECOND) a replacement recomputes
                             the residual in FP32 from the last FP64 one, r = r_64 - D x_32
                             (x_32: the solution accumulated since), until |r| has dropped
