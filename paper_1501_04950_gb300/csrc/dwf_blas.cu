@@ -295,8 +295,16 @@ __global__ void __launch_bounds__(kBlasThreads) px_update_kernel(
 // from z and p of those pairs as well.  Used by the CG on the tuned path, whose
 // D_bb pass A then hops B p directly.  p_old and p_new are different buffers
 // (neighbouring pairs of p_old are read while p_new is written).
+// FP32 fields: two CTAs per SM (128 registers, 48 bytes spilled) so that one
+// CTA's loads overlap the other's stores; the other combinations would spill
+// hundreds of bytes at that cap and keep one CTA per SM.
 template <class SPX, class SP>
-__global__ void __launch_bounds__(kBlasThreads) pxb_update_kernel(
+constexpr int pxb_min_blocks() {
+  return SP::kPrec == P32 && SPX::kPrec == P32 ? 2 : 1;
+}
+
+template <class SPX, class SP>
+__global__ void __launch_bounds__(kBlasThreads, (pxb_min_blocks<SPX, SP>())) pxb_update_kernel(
     const Geom g, void* x, const void* p, void* pnew, void* bp, const void* z, const double* a_ptr,
     const double* num, const double* den, int sstride, size_t stride_x, size_t stride,
     const typename SP::T* bdiag, const typename SP::T* boff, size_t cstride, const int* active,
@@ -316,13 +324,17 @@ __global__ void __launch_bounds__(kBlasThreads) pxb_update_kernel(
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < NP; m += gridDim.x * blockDim.x) {
     const int t = m % half, base = m - t;
     const int mp = base + (t == 0 ? half - 1 : t - 1), mn = base + (t + 1 == half ? 0 : t + 1);
-    Spinor<T> pv[2], zv[2], pl[2], zl[2], pu[2], zu[2];
+    // the slice below the pair (lane 1 of pair mp) enters through its v+ half,
+    // the slice above (lane 0 of pair mn) through its v- half; 16-bit storage
+    // loads all 12 components of those slices (the scale of their stored p_new)
+    const int n_below = 2 * mp + 1, n_above = 2 * mn;
+    Spinor<T> pv[2], zv[2], pl, zl, pu, zu;
     SP::load_pair(pb, m, NP, pv[0], pv[1]);
     SP::load_pair(zb, m, NP, zv[0], zv[1]);
-    SP::load_pair(pb, mp, NP, pl[0], pl[1]);
-    SP::load_pair(zb, mp, NP, zl[0], zl[1]);
-    SP::load_pair(pb, mn, NP, pu[0], pu[1]);
-    SP::load_pair(zb, mn, NP, zu[0], zu[1]);
+    SP::load_chir(pb, n_below, g.N5, 0, pl);
+    SP::load_chir(zb, n_below, g.N5, 0, zl);
+    SP::load_chir(pb, n_above, g.N5, 1, pu);
+    SP::load_chir(zb, n_above, g.N5, 1, zu);
     if (do_x) {
       Spinor<TX> xv[2];
       SPX::load_pair(reinterpret_cast<const char*>(x) + offx, m, NP, xv[0], xv[1]);
@@ -340,8 +352,10 @@ __global__ void __launch_bounds__(kBlasThreads) pxb_update_kernel(
 #pragma unroll
       for (int l = 0; l < 2; l++)
         q[l].c[k] = cmake(fma(beta, pv[l].c[k].re, zv[l].c[k].re), fma(beta, pv[l].c[k].im, zv[l].c[k].im));
-      qb.c[k] = cmake(fma(beta, pl[1].c[k].re, zl[1].c[k].re), fma(beta, pl[1].c[k].im, zl[1].c[k].im));
-      qa.c[k] = cmake(fma(beta, pu[0].c[k].re, zu[0].c[k].re), fma(beta, pu[0].c[k].im, zu[0].c[k].im));
+      if (SP::kScaled || k < 6)
+        qb.c[k] = cmake(fma(beta, pl.c[k].re, zl.c[k].re), fma(beta, pl.c[k].im, zl.c[k].im));
+      if (SP::kScaled || k >= 6)
+        qa.c[k] = cmake(fma(beta, pu.c[k].re, zu.c[k].re), fma(beta, pu.c[k].im, zu.c[k].im));
     }
     SP::store_pair(reinterpret_cast<char*>(pnew) + off, m, NP, q[0], q[1]);
     if constexpr (SP::kScaled) {
