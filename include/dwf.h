@@ -125,10 +125,12 @@ typedef struct {
   int applies_dag;       /* inner-precision D_bb^+ applies                             */
   int applies_fp64;      /* FP64 D_bb applies (true residuals)                          */
   int kernel_launches;   /* CUDA kernels the solve launched                             */
-  double apply_ms;       /* device time of the batch's inner D_bb applies (opt.profile = 1) */
+  double apply_ms;       /* device time of the batch's timed inner D_bb applies (opt.profile
+                            = 1: the applies of the first iteration after each poll)     */
   double apply_dag_ms;   /* same for the D_bb^+ applies                                  */
   int applies_fp32;      /* FP32 D_bb applies: residual replacements of FP16/BF16 solves
                             between two FP64 ones                                       */
+  int applies_timed;     /* D_bb (and D_bb^+) applies covered by apply_ms (apply_dag_ms) */
 } dwf_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -41,7 +41,8 @@ class Stats(ctypes.Structure):
                 ("seconds", ctypes.c_double), ("applies", ctypes.c_int),
                 ("applies_dag", ctypes.c_int), ("applies_fp64", ctypes.c_int),
                 ("kernel_launches", ctypes.c_int), ("apply_ms", ctypes.c_double),
-                ("apply_dag_ms", ctypes.c_double), ("applies_fp32", ctypes.c_int)]
+                ("apply_dag_ms", ctypes.c_double), ("applies_fp32", ctypes.c_int),
+                ("applies_timed", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
