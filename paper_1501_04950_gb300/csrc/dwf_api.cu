@@ -1762,10 +1762,19 @@ int dwf_cgne_solve_multi(dwf_solve_job* jobs, int njobs, dwf_stream s) {
     J.status = solve_5d(J.handle, J.src4d, J.prop4d, J.sol5d, J.nrhs, J.alphas, J.stats,
                         reinterpret_cast<dwf_stream>(J.handle->cstream), J.handle->m, 1.0);
   };
+  // one thread per job beyond the first; a job whose thread cannot be started
+  // runs on the calling thread (no exception crosses the C ABI)
   std::vector<std::thread> pool;
-  pool.reserve(njobs - 1);
-  for (int i = 1; i < njobs; i++) pool.emplace_back(run, i);
+  std::vector<int> inline_jobs;
+  for (int i = 1; i < njobs; i++) {
+    try {
+      pool.emplace_back(run, i);
+    } catch (...) {
+      inline_jobs.push_back(i);
+    }
+  }
   run(0);
+  for (int i : inline_jobs) run(i);
   for (auto& t : pool) t.join();
   int rc = DWF_OK;
   for (int i = 0; i < njobs && rc == DWF_OK; i++) rc = jobs[i].status;

@@ -37,3 +37,16 @@ def test_binding_fails_loudly_without_library(tmp_path):
     from paper_1501_04950_gb300 import dwf
     with pytest.raises(RuntimeError):
         dwf.load_library(str(tmp_path / "missing.so"))
+
+
+def test_multi_solve_rejects_bad_arguments_before_any_cuda_call():
+    """dwf_cgne_solve_multi checks its job list on the host first: an empty list or
+    a job without a handle is refused with DWF_ERR_INVALID_ARG and a message for
+    the calling thread (no GPU is touched, so this runs on any machine)."""
+    from paper_1501_04950_gb300 import dwf
+    lib = dwf.lib()
+    assert lib.dwf_cgne_solve_multi(None, 0, None) == 1
+    assert lib.dwf_last_error(None) == b"bad argument"
+    jobs = (dwf.SolveJobC * 2)()
+    assert lib.dwf_cgne_solve_multi(jobs, 2, None) == 1
+    assert lib.dwf_last_error(None) == b"job without a handle"
