@@ -71,11 +71,13 @@ enum { DWF_FP64 = 0, DWF_FP32 = 1, DWF_FP16 = 2, DWF_BF16 = 3 };
 
 /* Solver variants of dwf_cgne_solve. */
 enum {
-  DWF_SOLVER_RELIABLE = 0, /* inner precision CG with FP64 reliable updates (default);
-                              with BF16 inner fields the recurrence restarts at every
-                              update (as DWF_SOLVER_DEFECT), and with any precision it
-                              restarts after an update that gained < 10%; five such
-                              updates in a row end the solve (DWF_ERR_NOT_CONVERGED) */
+  DWF_SOLVER_RELIABLE = 0, /* inner precision CG with FP64 reliable updates (default;
+                              FP16/BF16 fields add FP32 ones in between, see
+                              reliable_delta); with BF16 inner fields the recurrence
+                              restarts at every update (as DWF_SOLVER_DEFECT), and with
+                              any precision it restarts after an FP64 update that gained
+                              < 10%; five such updates in a row end the solve
+                              (DWF_ERR_NOT_CONVERGED) */
   DWF_SOLVER_DEFECT = 1,   /* FP64 defect correction around restarted inner CG      */
   DWF_SOLVER_FP64 = 2      /* plain FP64 CG on the normal equations                 */
 };
@@ -200,9 +202,10 @@ int dwf_apply_dalpha(dwf_handle h, double* out_full, const double* in_full, doub
  * sides that share every kernel launch (each with its own alpha, scalars and
  * convergence; converged ones are masked off).  With rhs_block = 0 a built-in
  * autotuner times the batched D_bb apply for block sizes that fit in free
- * device memory, and for the two neighbour staging variants, and keeps the
- * fastest per right-hand side (cached per lattice, Ls, precision and nrhs in
- * the process, and in the file named by DWF_AUTOTUNE_CACHE if set).  The CG
+ * device memory, for the two CTA tiles of the hop kernels and for the two
+ * neighbour staging variants, and keeps the fastest per right-hand side
+ * (cached per lattice, Ls, precision and nrhs in the handle, and in the file
+ * named by DWF_AUTOTUNE_CACHE if set).  The CG
  * iterations between two convergence polls (check_every, rounded up to even)
  * are captured once as a CUDA graph and replayed.  All solver work runs on a
  * stream owned by the handle; the call first waits for the caller's stream. */
