@@ -54,21 +54,31 @@ def test_multi_solve_rejects_bad_arguments_before_any_cuda_call():
 
 def test_header_is_c99_and_matches_the_binding(tmp_path):
     """include/dwf.h compiles as strict C99 (C callers are part of the boundary),
-    and the option, stats and job structs have the sizes the ctypes binding uses."""
+    and the option, stats and job structs have the sizes and field offsets that
+    the ctypes binding uses."""
     import shutil
     import subprocess
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
+    from paper_1501_04950_gb300 import dwf
+    structs = [("dwf_options", dwf.Options), ("dwf_stats", dwf.Stats),
+               ("dwf_solve_job", dwf.SolveJobC)]
+    lines = ['#include "dwf.h"', "#include <stddef.h>", "#include <stdio.h>", "int main(void) {"]
+    for cname, cls in structs:
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % cname)
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (cname, fname))
+    lines += ["  return 0;", "}"]
     src = tmp_path / "hdr.c"
-    src.write_text('#include "dwf.h"\n#include <stdio.h>\n'
-                   'int main(void) { printf("%zu %zu %zu\\n", sizeof(dwf_options), '
-                   'sizeof(dwf_stats), sizeof(dwf_solve_job)); return 0; }\n')
+    src.write_text("\n".join(lines) + "\n")
     exe = tmp_path / "hdr"
     subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
                     "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
-    sizes = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
-                                            text=True).stdout.split()]
-    from paper_1501_04950_gb300 import dwf
-    assert sizes == [ctypes.sizeof(dwf.Options), ctypes.sizeof(dwf.Stats),
-                     ctypes.sizeof(dwf.SolveJobC)]
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True,
+                                          text=True).stdout.split()]
+    want = []
+    for _, cls in structs:
+        want.append(ctypes.sizeof(cls))
+        want += [getattr(cls, fname).offset for fname, _ in cls._fields_]
+    assert got == want
