@@ -180,3 +180,34 @@ def test_transposed_force_outer_product_is_caught(monkeypatch):
     outer = oracle.force._outer
     monkeypatch.setattr(oracle.force, "_outer", lambda a, b: np.swapaxes(outer(a, b), -1, -2))
     _fails(pins_force.test_force_vs_finite_differences_raw_entries)
+
+
+# --- App. A overlap, row scaling, single-site evaluator ------------------------------
+
+def test_sign_function_flip_is_caught(monkeypatch):
+    """eps of Eq. polar with the two products exchanged (eps -> -eps)."""
+    import oracle.overlap
+    tanh_form = oracle.overlap.sign_tanh_form
+    monkeypatch.setattr(oracle.overlap, "sign_tanh_form",
+                        lambda dwm, g5, b, c: -tanh_form(dwm, g5, b, c))
+    _fails(pins_schur.test_propagator_equals_overlap_inverse, "mobius", 1.0)
+
+
+def test_row_scaling_condition_reversed_is_caught(monkeypatch):
+    """Rows scaled where b_s + c_s < 1 instead of > 1."""
+    def row_scale(self):
+        a = self.b + self.c
+        return np.where(a < 1.0, 1.0 / a, 1.0)
+
+    monkeypatch.setattr(oracle.schur.DWFSystem, "row_scale", row_scale)
+    _fails(pins_schur.test_row_scale_factors)
+
+
+def test_pointwise_neighbour_direction_is_caught(monkeypatch):
+    """The single-site evaluator stepping to x - mu where it means x + mu."""
+    import oracle.pointwise
+    import test_oracle_pointwise as pins_pointwise
+    shift = oracle.pointwise._SiteOps._shift
+    monkeypatch.setattr(oracle.pointwise._SiteOps, "_shift",
+                        lambda self, c, mu, d: shift(self, c, mu, -d))
+    _fails(pins_pointwise.test_pointwise_matches_whole_lattice, 1.0, 0)
