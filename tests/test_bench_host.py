@@ -1,5 +1,6 @@
 """Host-side measurement logic of bench.py (no GPU): the algorithmic byte model,
-the traffic record's source-hash gate and the clock / throttle-reason parsing."""
+the traffic record's source-hash gate, the clock / throttle-reason parsing, the
+sign-error closed form and the JSON line of the oracle (reference) arm."""
 import json
 import os
 import sys
@@ -57,3 +58,25 @@ def test_sign_error_matches_zolotarev_ripple():
     q = [abs(1 - 2 * x) / (1 + 2 * x) for x in (0.05, 6.0)]
     closed = max(2 * v ** L / (1 + v ** L) for v in q)
     assert abs(bench.sign_error(np.full(L, 2.0)) - closed) < 1e-6 * closed
+
+
+def test_reference_arm_json_contract():
+    """bench.py --impl reference (the oracle arm) prints one JSON line with the
+    contract's keys on rank 0 and nothing on the other ranks."""
+    import subprocess
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+           "--warmup", "3"]
+    out = subprocess.run(cmd, check=True, capture_output=True, text=True, cwd=ROOT).stdout
+    lines = [l for l in out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert d["e2e"]["value"] == d["value"] and d["cpu_baseline"]["value"] == d["value"]
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    other = subprocess.run(cmd, check=True, capture_output=True, text=True, cwd=ROOT, env=env)
+    assert other.stdout.strip() == ""
